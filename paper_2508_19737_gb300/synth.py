@@ -1,0 +1,228 @@
+"""Seeded synthetic inputs: degree-corrected stochastic block model (DC-SBM) graphs.
+
+This module only draws inputs. It holds none of the method's arithmetic, imports
+neither the CUDA library nor the CPU checker, and both sides are fed from it.
+
+The paper evaluates on the IEEE HPEC Graph Challenge graphs (Sec. IV-A, Table I:
+planted blocks, heterogeneous block sizes, power-law degrees, mean degree ~40).
+Those files are not available here, so a seeded DC-SBM with the same kind of
+structure stands in for them:
+
+* node propensities theta_i from a power law p(x) ~ x^-gamma on [1, 100]
+  (inverse CDF);
+* block sizes equal (largest-remainder split) or Dirichlet(alpha) * N rounded
+  by largest remainder, every block non-empty;
+* M = round(N * mean_deg / 2) undirected edge draws with
+  P(u, v) ~ theta_u theta_v w(b_u, b_v), w = ratio inside a block and 1 across:
+  u is drawn with weight theta_u (ratio Th_{b_u} + Th_tot - Th_{b_u}), then the
+  draw is intra-block with probability ratio Th_{b_u} / (ratio Th_{b_u} +
+  Th_tot - Th_{b_u}), and v is drawn with weight theta_v inside the chosen side.
+  Self-loops and repeated pairs are left in; the CSR build drops and merges them.
+* node labels: a random permutation ("random"), or block-major with nodes in
+  decreasing drawn degree inside each block ("block_degree").
+"""
+import numpy as np
+
+__all__ = ["DCSBM", "dcsbm", "powerlaw_propensities", "block_sizes", "batch_dcsbm",
+           "split_increments", "log_uniform_sizes"]
+
+
+class DCSBM:
+    """A drawn graph: int32 edge arrays (src, dst), N, and per-node block labels."""
+
+    def __init__(self, src, dst, N, blocks, theta, seed, params):
+        self.src = src
+        self.dst = dst
+        self.N = N
+        self.blocks = blocks
+        self.theta = theta
+        self.seed = seed
+        self.params = params
+
+    @property
+    def M(self):
+        return int(self.src.size)
+
+    def __repr__(self):
+        return f"DCSBM(N={self.N}, M={self.M}, blocks={int(self.blocks.max()) + 1}, seed={self.seed})"
+
+
+def powerlaw_propensities(rng, n, gamma, lo=1.0, hi=100.0):
+    """n draws from p(x) ~ x^-gamma on [lo, hi] (inverse CDF, gamma != 1)."""
+    a = 1.0 - gamma
+    u = rng.random(n)
+    return (lo ** a + u * (hi ** a - lo ** a)) ** (1.0 / a)
+
+
+def _largest_remainder(p, N):
+    raw = p * N
+    base = np.floor(raw).astype(np.int64)
+    short = N - int(base.sum())
+    if short > 0:
+        order = np.argsort(-(raw - base), kind="stable")
+        base[order[:short]] += 1
+    return base
+
+
+def block_sizes(rng, N, B, dirichlet_alpha=None):
+    """Sizes of B non-empty blocks summing to N."""
+    if B > N:
+        raise ValueError("more blocks than nodes")
+    if dirichlet_alpha is None:
+        p = np.full(B, 1.0 / B)
+    else:
+        p = rng.dirichlet(np.full(B, float(dirichlet_alpha)))
+    sizes = _largest_remainder(p, N)
+    while (sizes == 0).any():  # give every empty block one node from the largest
+        k = int(np.argmin(sizes))
+        j = int(np.argmax(sizes))
+        sizes[k] += 1
+        sizes[j] -= 1
+    return sizes
+
+
+def dcsbm(N, B, mean_deg, gamma, ratio, seed=0, dirichlet_alpha=None, order="random",
+          theta_range=(1.0, 100.0)):
+    """Draw one DC-SBM graph (see the module docstring)."""
+    rng = np.random.default_rng(seed)
+    sizes = block_sizes(rng, N, B, dirichlet_alpha)
+    starts = np.concatenate([[0], np.cumsum(sizes)])
+    blk = np.repeat(np.arange(B), sizes)  # internal order: block-contiguous
+    th = powerlaw_propensities(rng, N, gamma, *theta_range)
+    cum = np.concatenate([[0.0], np.cumsum(th)])
+    Tb = cum[starts[1:]] - cum[starts[:-1]]
+    Ttot = cum[-1]
+    M = int(round(N * mean_deg / 2.0))
+
+    # u with weight theta_u * (ratio*Tb + Ttot - Tb)
+    wu = th * (ratio * Tb[blk] + Ttot - Tb[blk])
+    cw = np.cumsum(wu)
+    u = np.searchsorted(cw, rng.random(M) * cw[-1], side="right")
+    u = np.minimum(u, N - 1)
+    bu = blk[u]
+    p_in = ratio * Tb[bu] / (ratio * Tb[bu] + Ttot - Tb[bu])
+    intra = rng.random(M) < p_in
+    x = rng.random(M)
+    s0 = cum[starts[bu]]
+    s1 = cum[starts[bu + 1]]
+    # intra: a point in [cum[start_b], cum[end_b]); inter: a point in the rest
+    y_in = s0 + x * (s1 - s0)
+    y_out = x * (Ttot - Tb[bu])
+    y_out = np.where(y_out >= s0, y_out + Tb[bu], y_out)
+    y = np.where(intra, y_in, y_out)
+    v = np.searchsorted(cum, y, side="right") - 1
+    v = np.clip(v, 0, N - 1)
+    lo_b = starts[bu]
+    hi_b = starts[bu + 1] - 1
+    v = np.where(intra, np.clip(v, lo_b, hi_b), v)  # rounding at a block edge
+
+    if order == "random":
+        label = rng.permutation(N)
+    elif order == "block_degree":
+        drawn = np.bincount(u, minlength=N) + np.bincount(v, minlength=N)
+        # block-major, then decreasing drawn degree, then internal index
+        idx = np.lexsort((np.arange(N), -drawn, blk))
+        label = np.empty(N, dtype=np.int64)
+        label[idx] = np.arange(N)
+    elif order == "internal":
+        label = np.arange(N)
+    else:
+        raise ValueError(order)
+    src = label[u].astype(np.int32)
+    dst = label[v].astype(np.int32)
+    blocks = np.empty(N, dtype=np.int32)
+    blocks[label] = blk
+    theta_l = np.empty(N)
+    theta_l[label] = th
+    params = dict(N=N, B=B, mean_deg=mean_deg, gamma=gamma, ratio=ratio,
+                  dirichlet_alpha=dirichlet_alpha, order=order)
+    return DCSBM(src, dst, N, blocks, theta_l, seed, params)
+
+
+def log_uniform_sizes(rng, n, lo, hi):
+    """n integers log-uniform on [lo, hi]."""
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), size=n)).round().astype(np.int64)
+
+
+def batch_dcsbm(G, n_lo, n_hi, deg_lo, deg_hi, gamma, ratio, seed=0, block_exp=0.4):
+    """G independent graphs: N log-uniform on [n_lo, n_hi], blocks = round(N^block_exp),
+    mean degree uniform on [deg_lo, deg_hi]; graph g uses SeedSequence(seed).spawn(G)[g]."""
+    ss = np.random.SeedSequence(seed)
+    rng = np.random.default_rng(ss)
+    Ns = log_uniform_sizes(rng, G, n_lo, n_hi)
+    degs = rng.uniform(deg_lo, deg_hi, size=G)
+    kids = ss.spawn(G)
+    out = []
+    for g in range(G):
+        N = int(Ns[g])
+        B = max(1, int(round(N ** block_exp)))
+        out.append(dcsbm(N, B, float(degs[g]), gamma, ratio, seed=kids[g]))
+    return out
+
+
+def split_increments(graph, T=10, mode="random", seed=0):
+    """Cut a drawn graph into T edge increments.
+
+    mode="random": edges in a uniformly random order, T equal slices; every
+    slice carries the full node count N.
+    mode="snowball": nodes ordered by breadth-first search from a random start
+    (unreached nodes appended in random order), split into T equal node groups
+    V_1..V_T (the snowball model of Sec. II); increment t holds the edges whose
+    later-visited endpoint lies in V_t, and node ids are relabelled to the visit
+    order so that the nodes present after step t are 0..N_t-1.
+    Returns a list of (src, dst, N_t).
+    """
+    rng = np.random.default_rng(seed)
+    src = graph.src.astype(np.int64)
+    dst = graph.dst.astype(np.int64)
+    N = graph.N
+    if mode == "random":
+        perm = rng.permutation(src.size)
+        cuts = np.linspace(0, src.size, T + 1).round().astype(np.int64)
+        return [(src[perm[a:b]].astype(np.int32), dst[perm[a:b]].astype(np.int32), N)
+                for a, b in zip(cuts[:-1], cuts[1:])]
+    if mode != "snowball":
+        raise ValueError(mode)
+    # adjacency lists for BFS
+    keep = src != dst
+    u = np.concatenate([src[keep], dst[keep]])
+    v = np.concatenate([dst[keep], src[keep]])
+    o = np.argsort(u, kind="stable")
+    u, v = u[o], v[o]
+    ptr = np.searchsorted(u, np.arange(N + 1))
+    visit = np.full(N, -1, dtype=np.int64)
+    order = []
+    start = int(rng.integers(N))
+    rest = rng.permutation(N)
+    ri = 0
+    frontier = [start]
+    visit[start] = 0
+    order.append(start)
+    while len(order) < N:
+        nxt = []
+        for a in frontier:
+            for b in v[ptr[a]:ptr[a + 1]]:
+                if visit[b] < 0:
+                    visit[b] = len(order)
+                    order.append(int(b))
+                    nxt.append(int(b))
+        if not nxt:
+            while ri < N and visit[rest[ri]] >= 0:
+                ri += 1
+            if ri >= N:
+                break
+            b = int(rest[ri])
+            visit[b] = len(order)
+            order.append(b)
+            nxt = [b]
+        frontier = nxt
+    pos = visit  # relabel: node -> visit position
+    su, sv = pos[src], pos[dst]
+    later = np.maximum(su, sv)
+    bounds = np.linspace(0, N, T + 1).round().astype(np.int64)
+    step = np.searchsorted(bounds[1:], later, side="right")
+    out = []
+    for t in range(T):
+        m = step == t
+        out.append((su[m].astype(np.int32), sv[m].astype(np.int32), int(bounds[t + 1])))
+    return out

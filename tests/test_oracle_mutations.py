@@ -1,0 +1,93 @@
+"""The oracle pins are not vacuous: plant a plausible mistake in the oracle (on
+the CPU, by patching one of its functions) and check that some pin fails."""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.fp64 as off
+import oracle.philox as oph
+from tests import test_oracle_pins as pins
+
+# pins that take no fixtures/parameters, plus parametrised ones with fixed args
+PIN_CALLS = [
+    lambda: pins.test_one_layer_edgeless_graph_closed_form(),
+    lambda: pins.test_one_layer_path_graph_closed_form(),
+    lambda: pins.test_zero_layers_is_sigmoid_of_input(),
+    lambda: pins.test_constant_column_maps_to_zero(),
+    lambda: pins.test_degree_correction_closed_forms(),
+    lambda: pins.test_ffp_equals_brute_force(1, -1.5, 4),
+    lambda: pins.test_ffp_equals_brute_force(3, 2.0, 2),
+    lambda: pins.test_eq3_spectral_equals_spatial(-1.5, 1.0, 0.1),
+    lambda: pins.test_eq3_spectral_equals_spatial(3.0, -0.5, 0.7),
+    lambda: pins.test_corrected_laplacian_on_sqrt_degree_vector(-1.5),
+    lambda: pins.test_csr_equals_brute_force_sets(0),
+    lambda: pins.test_philox_matches_numpy_bitgenerator([5, 7, 0, 0], [123, 456]),
+    lambda: pins.test_uniform_map_closed_form(),
+    lambda: pins.test_box_muller_closed_form(),
+    lambda: pins.test_theta_is_gaussian_with_variance_one_over_d(),
+]
+
+
+def _some_pin_fails():
+    for call in PIN_CALLS:
+        try:
+            call()
+        except (AssertionError, ValueError, IndexError):
+            return True
+    return False
+
+
+def _mut_dinv_same_side(row_ptr, col, dinv):
+    # D^{-1} A instead of D^{-1/2} A D^{-1/2}
+    import scipy.sparse as sp
+    N = len(row_ptr) - 1
+    A = sp.csr_matrix((np.ones(len(col)), col, row_ptr), shape=(N, N))
+    return (sp.diags(np.asarray(dinv) ** 2) @ A).tocsr()
+
+
+MUTATIONS = {
+    "self term dropped": ("conv", lambda Ahat, Z, alpha=1.0, theta=0.1: alpha * (Ahat @ Z)),
+    "alpha sign flipped": ("conv", lambda Ahat, Z, alpha=1.0, theta=0.1: theta * Z - alpha * (Ahat @ Z)),
+    "tau ignored": ("degree_correction", lambda deg, tau, eps=1e-3: np.asarray(deg, dtype=float)),
+    "eps clamp dropped": ("degree_correction", lambda deg, tau, eps=1e-3: np.asarray(deg, dtype=float) + tau),
+    "dinv on one side": ("normalized_adjacency", _mut_dinv_same_side),
+    "ddof 0": ("znorm", lambda T, ddof=1: off.__dict__["_orig_znorm"](T, 0)),
+    "no centring": ("znorm", lambda T, ddof=1: (lambda z, m, s: (T / np.where(s > 0, s, 1), m * 0, s))(*off.__dict__["_orig_znorm"](T, ddof))),
+    "sigmoid sign": ("sigmoid", lambda x: 1.0 / (1.0 + np.exp(np.asarray(x, dtype=float)))),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_ffp_mistake_is_caught(monkeypatch, name):
+    fn, impl = MUTATIONS[name]
+    monkeypatch.setitem(off.__dict__, "_orig_znorm", off.znorm)
+    monkeypatch.setattr(off, fn, impl)
+    monkeypatch.setattr(oracle, fn, impl, raising=False)
+    assert _some_pin_fails(), f"no pin caught: {name}"
+
+
+def test_planted_tanh_removal_is_caught(monkeypatch):
+    class _NP:  # numpy facade whose tanh is the identity
+        def __getattr__(self, k):
+            return getattr(np, k)
+
+        @staticmethod
+        def tanh(x):
+            return x
+    monkeypatch.setattr(off, "np", _NP())
+    assert _some_pin_fails()
+
+
+@pytest.mark.parametrize("name", ["multiplier", "key bump", "word order", "uniform offset"])
+def test_planted_generator_mistake_is_caught(monkeypatch, name):
+    if name == "multiplier":
+        monkeypatch.setattr(oph, "PHILOX_M0", np.uint64(0xD2E7470EE14C6C95))
+    elif name == "key bump":
+        monkeypatch.setattr(oph, "PHILOX_W1", np.uint64(0x9E3779B97F4A7C15))
+    elif name == "word order":
+        orig = oph.uniforms_from_words
+        monkeypatch.setattr(oph, "uniforms_from_words", lambda x: orig(x)[..., ::-1])
+    elif name == "uniform offset":
+        monkeypatch.setattr(oph, "uniforms_from_words",
+                            lambda x: ((np.asarray(x, dtype=np.uint64)[..., [0, 0, 1, 1, 2, 2, 3, 3]] >> np.uint64(40))).astype(float) * 2.0 ** -24)
+    assert _some_pin_fails()
