@@ -1,0 +1,362 @@
+"""Benchmark of the InfraredGP FFP hot path on GB300 (one JSON line on rank 0).
+
+A step is one pass of the whole hot path over one synthetic graph: CSR
+construction from the device-resident edge list, Eq. 1 degree factors, the
+Theta draw, L Eq. 4 layers and the sigmoid output (Alg. 1, lines 1-6). The
+metric is edge*dim*layer/s = nnz * d * L per step / step time, nnz counting
+the directed CSR entries (twice the undirected edges).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the FP64 oracle on the host cores
+
+Multi-GPU (torchrun): every rank runs an independent replica of the workload
+(the FFP of one graph does not shard); value = units of all ranks / max time.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2508_19737_gb300 import synth  # noqa: E402
+
+METRIC = "FFP edge*dim*layer/s"
+UNIT = "edge*dim*layer/s"
+L2_BYTES = 129 * 1024 * 1024
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_layer_dcsbm-2m.json")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="dcsbm-2m", choices=sorted(synth.WORKLOADS))
+    p.add_argument("--storage", default=None, choices=[None, "f32", "bf16"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=None)
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def layer_bytes(N, nnz, d, sb):
+    """Algorithmic bytes of one Eq. 4 layer launch: col + row_ptr + dinv read once,
+    T^(l-1) read once, T^(l) written once."""
+    return 4 * nnz + 4 * (N + 1) + 4 * N + 2 * N * d * sb
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2508_19737_gb300", "csrc", "ffp.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, storage):
+    """Per-launch DRAM bytes of k_layer from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    try:
+        with open(PROFILE_SUMMARY) as f:
+            j = json.load(f)
+        e = j["entries"][f"{workload}/{storage}"]
+        if e.get("ffp_cu_sha256_16") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+class OracleSample:
+    """The FP64 oracle, as it stands, timed on a bounded sample of the workload: one Eq. 4
+    layer (oracle conv + tanh + ZNorm statistics) over a leading slice of the rows of the
+    workload graph. The oracle's CSR, Eq. 1 factors and Theta are prepared once, untimed;
+    the slice is sized once so that a pass takes about `budget_s`."""
+
+    def __init__(self, g, wl, budget_s):
+        import oracle
+        self.oracle = oracle
+        self.rp, col = oracle.build_csr(g.src, g.dst, g.N)
+        dinv = oracle.inv_sqrt_degrees(oracle.degree_correction(oracle.degrees(self.rp), wl["tau"]))
+        self.Ahat = oracle.normalized_adjacency(self.rp, col, dinv)
+        self.d = wl["d"]
+        self.N = g.N
+        self.X = oracle.theta_input(0, g.N, self.d)
+        rows = min(g.N, 20000)
+        while True:
+            dt = self._pass(rows)
+            if dt >= budget_s or rows == g.N:
+                break
+            rows = min(g.N, int(rows * max(1.5, 1.1 * budget_s / max(dt, 1e-3))))
+        self.rows = rows
+
+    def _pass(self, rows):
+        t0 = time.perf_counter()
+        T = np.tanh(self.oracle.conv_rows(self.Ahat, self.X, 0, rows, 1.0, 0.1))
+        self.oracle.znorm(T, 1)
+        return time.perf_counter() - t0
+
+    def rate(self):
+        dt = self._pass(self.rows)
+        return float(self.rp[self.rows]) * self.d / dt, dt
+
+    def describe(self, dt):
+        return (f"one Eq. 4 layer of the FP64 oracle (numpy/scipy, single thread) over rows 0..{self.rows - 1} of "
+                f"the {self.N}-node graph ({int(self.rp[self.rows])} of {int(self.rp[-1])} CSR entries, "
+                f"d={self.d}), {dt:.2f} s per pass")
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = synth.WORKLOADS[args.workload]
+    g = synth.workload_graph(args.workload)
+    budget = max(0.2, min(10.0, 90.0 / max(1, args.steps + args.warmup)))
+    smp = OracleSample(g, wl, budget)
+    rates, dts = [], []
+    for k in range(args.warmup + args.steps):
+        r, dt = smp.rate()
+        if k >= args.warmup:
+            rates.append(r)
+            dts.append(dt)
+    value = statistics.mean(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(dts), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, **wl["graph"], "d": wl["d"], "tau": wl["tau"], "L": wl["L"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": smp.describe(statistics.mean(dts))},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_19737_gb300 import api
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wl = synth.WORKLOADS[args.workload]
+    storage = args.storage or wl["storage"]
+    sb = 2 if storage == "bf16" else 4
+    d, tau, L = wl["d"], wl["tau"], wl["L"]
+    g = synth.workload_graph(args.workload)
+    N, M = g.N, g.M
+    src = torch.from_numpy(g.src).cuda()
+    dst = torch.from_numpy(g.dst).cuda()
+    out = torch.empty((N, d), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    opts = api.embed_opts(storage=storage)
+    probe = api.graph_build(src, dst, N)
+    _, nnz, maxdeg = probe.info()
+    probe.free()
+
+    def step(prof=None):
+        gr = api.graph_build(src, dst, N, stream=stream, profile=prof)
+        opts.profile = prof.handle if prof is not None else None
+        api.embed(gr, tau, L, d, 0, out=out, opts=opts, stream=stream)
+        gr.free()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    prof = api.Profile()
+    n0 = api.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(prof)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = api.launch_count() - n0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    phases = prof.read()
+    prof.close()
+    ms_step = ms / args.steps
+    units_step = float(nnz) * d * L
+    value = units_step * args.steps * world / (ms / 1e3)
+
+    # end to end through the public API: pinned host edges in, pinned host embeddings out
+    src_h = torch.from_numpy(g.src).pin_memory()
+    dst_h = torch.from_numpy(g.dst).pin_memory()
+    out_h = torch.empty((N, d), dtype=torch.float32).pin_memory()
+    e2e_steps = args.e2e_steps or max(3, min(args.steps, 20))
+
+    def step_e2e():
+        gr = api.graph_build(src_h, dst_h, N, stream=stream)
+        api.embed(gr, tau, L, d, 0, out=out_h, opts=opts, stream=stream)
+        gr.free()
+    opts.profile = None
+    step_e2e()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = units_step * e2e_steps * world / e2e_s
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    layer_ms, layer_n = phases["layer"]
+    avg_layer_s = layer_ms / max(layer_n, 1) / 1e3
+    lb = layer_bytes(N, nnz, d, sb)
+    peak, peak_src = peaks()
+    achieved = lb / avg_layer_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(args.workload, storage), "kernel": "k_layer",
+                "algorithmic_bytes_per_launch": lb, "avg_launch_ms": avg_layer_s * 1e3,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else
+                "fallback 6800 GB/s"}
+    ffp_ms = sum(phases[k][0] for k in ("dinv", "theta", "layer", "output")) / args.steps
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        smp = OracleSample(g, wl, 10.0)
+        rate, dt = smp.rate()
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": smp.describe(dt)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": storage, "data": "synthetic",
+        "config": {"workload": args.workload, **wl["graph"], "M_drawn": M, "nnz": int(nnz), "max_deg": int(maxdeg),
+                   "d": d, "tau": tau, "L": L, "storage": storage, "accumulate": "f32",
+                   "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (edge list %d MB, T %d MB each > 129 MB)" % (
+                       8 * M >> 20, N * d * sb >> 20) if N * d * sb > L2_BYTES else "working set may fit L2"},
+        "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+        "ffp_only": {"value": units_step / (ffp_ms / 1e3), "unit": UNIT,
+                     "what": "dinv + theta + L layers + output, CSR build excluded"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * M, "d2h_bytes_per_step": N * d * 4,
+                "steps": e2e_steps},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,161 @@
+/*
+ * igp.h -- C-ABI of the GB300 (sm_103a) library for InfraredGP's feed-forward
+ * propagation (FFP): Qin, Li, Cui, Pei, "InfraredGP: Efficient Graph
+ * Partitioning via Spectral Graph Neural Networks with Negative Corrections",
+ * arXiv 2508.19737.
+ *
+ * What the library computes (Alg. 1, lines 1-6):
+ *   A       symmetric binary adjacency of an undirected simple graph (Sec. II)
+ *   D_tau   Eq. 1 for tau < 0: deg_i - min(|tau|, deg_i - eps); deg_i + tau otherwise (Sec. I)
+ *   Z^(0)   Theta ~ N(0, 1/d), drawn from a seed on the device (Alg. 1, line 2)
+ *   Z^(l)   ZNorm(tanh(theta Z^(l-1) + alpha D_tau^{-1/2} A D_tau^{-1/2} Z^(l-1))), l = 1..L
+ *           (Eq. 2-4; the paper's low-pass filter is (alpha, theta) = (1, 0.1))
+ *   out     sigmoid(Z^(L)) (Eq. 4), optionally divided by its row L2 norm
+ *
+ * Conventions for every entry point:
+ *   - Node ids are 0-based int32 in [0, N). Edges are undirected; either or both
+ *     directions may be given; self-loops are dropped and repeated edges merged.
+ *   - A pointer argument may be host memory (pageable or pinned) or device memory
+ *     of the current CUDA device; the library asks the CUDA runtime which. Host
+ *     inputs are copied before the call returns; host outputs are complete when
+ *     the call returns.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Work on device
+ *     buffers is enqueued on it; a call whose outputs are all device buffers may
+ *     return before the work finishes.
+ *   - Nothing is thrown across the ABI. A non-zero igp_status is returned on error
+ *     and igp_last_error() gives a thread-local message. On error no output is
+ *     partially written by the host side and no handle is created.
+ *   - A handle may be used from any thread, but calls on the same handle must not
+ *     overlap.
+ */
+#ifndef IGP_H
+#define IGP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t igp_status;
+#define IGP_OK            0
+#define IGP_E_INVAL       1  /* bad argument: id out of range, size limits, unsupported d */
+#define IGP_E_NOMEM       2  /* device allocation failed */
+#define IGP_E_CUDA        3  /* a CUDA runtime call failed (message has the CUDA error) */
+#define IGP_E_TIMEOUT     4  /* a bounded device-side wait gave up */
+#define IGP_E_BUSY        5  /* resource held by another request */
+#define IGP_E_NOTREADY    6  /* polled work not finished yet */
+#define IGP_E_CANCELLED   7  /* request cancelled before it ran */
+#define IGP_E_UNSUPPORTED 8
+
+/* Storage type of the N x d layer activations T^(l) and of Theta. Accumulation is
+ * always fp32, degree factors are computed in fp64, the output is fp32. */
+#define IGP_STORE_F32  0
+#define IGP_STORE_BF16 1
+
+/* Phases timed by an igp_profile (device time between CUDA events). */
+#define IGP_PHASE_DINV   0  /* Eq. 1 degree factors (fp64 on the device) */
+#define IGP_PHASE_THETA  1  /* Theta generation (Alg. 1, line 2) */
+#define IGP_PHASE_LAYER  2  /* one Eq. 4 layer: gather-SpMM + tanh + column statistics */
+#define IGP_PHASE_OUTPUT 3  /* sigmoid(ZNorm(T^(L))) */
+#define IGP_PHASE_BUILD  4  /* whole CSR construction from an edge list */
+#define IGP_NUM_PHASES   5
+
+typedef struct igp_graph igp_graph;
+typedef struct igp_profile igp_profile;
+
+/* Options of one FFP. Fill with igp_embed_opts_init() and change fields. */
+typedef struct igp_embed_opts {
+  double alpha;        /* Eq. 2 slope; 1.0 (low-pass). Negative values give a high-pass filter. */
+  double theta;        /* Eq. 2 offset (the self term of Eq. 3); 0.1 */
+  double eps;          /* Eq. 1 clamp; 1e-3 */
+  double x_scale;      /* Theta = N(0,1) * x_scale; <= 0 means 1/sqrt(d) (the paper's N(0, 1/d)) */
+  int32_t znorm_ddof;  /* ZNorm standard deviation divisor N - ddof; 1 (0 allowed) */
+  int32_t storage;     /* IGP_STORE_F32 (default) or IGP_STORE_BF16 */
+  int32_t out_row_l2;  /* 1: divide each output row by its L2 norm; 0 (default) */
+  int32_t reserved0;
+  const void* x_in;    /* NULL: Theta from `seed`. Else a DEVICE pointer to N x d row-major values in
+                          the storage type, used as Z^(0) instead (not modified). */
+  igp_profile* profile;/* NULL, or a profile that records per-phase device times of this call */
+} igp_embed_opts;
+
+/* Library version string; never NULL. */
+const char* igp_version(void);
+
+/* Message of the last error on this thread ("" if none); owned by the library. */
+const char* igp_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process so far. */
+int64_t igp_launch_count(void);
+
+/* Defaults: alpha 1, theta 0.1, eps 1e-3, x_scale 1/sqrt(d), ddof 1, fp32 storage, no row L2. */
+void igp_embed_opts_init(igp_embed_opts* opts);
+
+/*
+ * Build the CSR adjacency of an undirected graph on the device (Sec. II: A is
+ * symmetric, binary, without self-loops). Columns of each row are sorted
+ * increasingly. Integer result, identical to sort + unique of the directed pairs.
+ *   src, dst : M node ids each (host or device), edge e = {src[e], dst[e]}
+ *   M        : 0 <= M < 2^30
+ *   N        : 1 <= N < 2^31 - 1
+ *   out      : receives a new graph handle (free with igp_graph_free)
+ * Errors: IGP_E_INVAL if an id is outside [0, N) (no handle is created),
+ * IGP_E_NOMEM, IGP_E_CUDA. Synchronises `stream` once (to size the column array).
+ */
+igp_status igp_graph_build(const int32_t* src, const int32_t* dst, int64_t M, int32_t N,
+                           void* stream, igp_graph** out);
+
+/* Same as igp_graph_build, recording the device time of the build in `profile` (may be NULL). */
+igp_status igp_graph_build_profiled(const int32_t* src, const int32_t* dst, int64_t M, int32_t N,
+                                    void* stream, igp_profile* profile, igp_graph** out);
+
+/* N, number of stored (directed) CSR entries nnz = sum of degrees, and the largest degree. */
+igp_status igp_graph_info(const igp_graph* g, int32_t* N, int64_t* nnz, int32_t* max_deg);
+
+/* Copy the CSR out: row_ptr[N+1] and col[nnz] (host or device; either may be NULL). */
+igp_status igp_graph_export(const igp_graph* g, int32_t* row_ptr, int32_t* col, void* stream);
+
+/* Eq. 1 degree factors D_tau^{-1/2} as fp32 (computed in fp64, IEEE sqrt and division, then
+ * rounded to nearest fp32), dinv[N] host or device. 0 where D_tau == 0 (tau = 0, isolated node). */
+igp_status igp_degree_factors(igp_graph* g, double tau, double eps, float* dinv, void* stream);
+
+/* Release a graph and its device memory. NULL is a no-op. The memory is returned to the library's
+ * pool in stream order after the last work issued on the handle; the call does not block. */
+void igp_graph_free(igp_graph* g);
+
+/*
+ * Theta of Alg. 1, line 2, exactly as igp_embed draws it, as fp32 [N][d] (host or device):
+ * Philox4x64-10 (Salmon et al., SC 2011) on counter (i, c/8, 0, 0) with key (seed, 0); its four
+ * 64-bit words are split into eight 32-bit halves w_k (low half first); u_k = ((w_k >> 8) + 1) 2^-24;
+ * Box-Muller on (u_{2p}, u_{2p+1}) in fp32 gives columns 8(c/8) + 0..7; times x_scale
+ * (<= 0: 1/sqrt(d)). d must be a multiple of 8.
+ */
+igp_status igp_generate_x(uint64_t seed, int32_t N, int32_t d, double x_scale, float* out, void* stream);
+
+/*
+ * One FFP (Alg. 1, lines 1-6) on graph g:
+ *   tau  : degree correction (Eq. 1 for tau < 0), any finite value
+ *   L    : number of layers, 0 <= L <= 10000 (L = 0 gives sigmoid(Theta))
+ *   d    : embedding width, one of 8, 16, 32, 64, 128
+ *   seed : Theta seed (ignored when opts->x_in is set)
+ *   out  : N x d fp32 row-major (host or device)
+ *   opts : NULL for defaults
+ * Errors: IGP_E_INVAL (bad d, L, tau, options), IGP_E_NOMEM, IGP_E_CUDA.
+ * Uses (and keeps, until igp_graph_free) a per-graph device workspace of about
+ * 2 N d storage-size bytes.
+ */
+igp_status igp_embed(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed, float* out,
+                     const igp_embed_opts* opts, void* stream);
+
+/* Per-phase device timing. Events are recorded on the call's stream around each phase. */
+igp_status igp_profile_create(igp_profile** p);
+void igp_profile_free(igp_profile* p);
+/* Wait for the recorded events, add their durations up per phase (ms) and count the launches per
+ * phase; both arrays have IGP_NUM_PHASES entries (either may be NULL). Clears the record. */
+igp_status igp_profile_read(igp_profile* p, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGP_H */

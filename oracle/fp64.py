@@ -30,7 +30,7 @@ import scipy.sparse as sp
 
 __all__ = [
     "build_csr", "degrees", "degree_correction", "inv_sqrt_degrees",
-    "normalized_adjacency", "conv", "znorm", "sigmoid", "round_bf16",
+    "normalized_adjacency", "conv", "conv_rows", "znorm", "sigmoid", "round_bf16",
     "ffp", "ffp_from_edges", "stream_snapshots", "dense_adjacency",
     "corrected_laplacian",
 ]
@@ -60,9 +60,8 @@ def build_csr(src, dst, N):
     keys = np.unique(u * np.int64(N) + v)  # sorted by (row, col), duplicates merged
     rows = keys // N
     col = keys % N
-    row_ptr = np.zeros(N + 1, dtype=np.int64)
-    np.add.at(row_ptr, rows + 1, 1)
-    row_ptr = np.cumsum(row_ptr)
+    counts = np.bincount(rows, minlength=N)  # row lengths
+    row_ptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
     return row_ptr, col
 
 
@@ -103,6 +102,11 @@ def normalized_adjacency(row_ptr, col, dinv):
 def conv(Ahat, Z, alpha=1.0, theta=0.1):
     """Eq. 3 in its spatial form: theta Z + alpha Ahat Z."""
     return theta * Z + alpha * (Ahat @ Z)
+
+
+def conv_rows(Ahat, Z, r0, r1, alpha=1.0, theta=0.1):
+    """Rows r0..r1-1 of Eq. 3 (the same definition as conv, on a row range)."""
+    return theta * Z[r0:r1] + alpha * (Ahat[r0:r1] @ Z)
 
 
 def znorm(T, ddof=1):

@@ -1,0 +1,273 @@
+"""ctypes binding over the C-ABI of libigp.so (include/igp.h), same names.
+
+Argument marshalling only: every step of the FFP runs in the library's CUDA
+kernels. Buffers may be numpy arrays (host) or torch tensors (host or CUDA);
+the library itself tells host from device pointers. Raises IgpError on a
+non-zero status and RuntimeError if the library has not been built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libigp.so")
+
+IGP_OK = 0
+IGP_E_INVAL = 1
+IGP_E_NOMEM = 2
+IGP_E_CUDA = 3
+IGP_E_TIMEOUT = 4
+IGP_E_BUSY = 5
+IGP_E_NOTREADY = 6
+IGP_E_CANCELLED = 7
+IGP_E_UNSUPPORTED = 8
+
+IGP_STORE_F32 = 0
+IGP_STORE_BF16 = 1
+
+IGP_PHASE_DINV = 0
+IGP_PHASE_THETA = 1
+IGP_PHASE_LAYER = 2
+IGP_PHASE_OUTPUT = 3
+IGP_PHASE_BUILD = 4
+IGP_NUM_PHASES = 5
+PHASE_NAMES = ["dinv", "theta", "layer", "output", "build"]
+
+STORAGE = {"f32": IGP_STORE_F32, "bf16": IGP_STORE_BF16}
+
+
+class IgpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"igp status {status}: {msg}")
+        self.status = status
+
+
+class EmbedOpts(ctypes.Structure):
+    _fields_ = [
+        ("alpha", ctypes.c_double),
+        ("theta", ctypes.c_double),
+        ("eps", ctypes.c_double),
+        ("x_scale", ctypes.c_double),
+        ("znorm_ddof", ctypes.c_int32),
+        ("storage", ctypes.c_int32),
+        ("out_row_l2", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("x_in", ctypes.c_void_p),
+        ("profile", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "igp_version": (ctypes.c_char_p, []),
+    "igp_last_error": (ctypes.c_char_p, []),
+    "igp_launch_count": (ctypes.c_int64, []),
+    "igp_embed_opts_init": (None, [ctypes.POINTER(EmbedOpts)]),
+    "igp_graph_build": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "igp_graph_build_profiled": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "igp_graph_info": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
+    "igp_graph_export": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "igp_degree_factors": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
+    "igp_graph_free": (None, [ctypes.c_void_p]),
+    "igp_generate_x": (ctypes.c_int32, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "igp_embed": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(EmbedOpts), ctypes.c_void_p]),
+    "igp_profile_create": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_void_p)]),
+    "igp_profile_free": (None, [ctypes.c_void_p]),
+    "igp_profile_read": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int64)]),
+}
+
+
+def lib():
+    """Load libigp.so (once). Raises if it has not been built: there is no fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2508_19737_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status):
+    if status != IGP_OK:
+        raise IgpError(status, lib().igp_last_error().decode())
+
+
+def _ptr(x):
+    """Raw address of a numpy array or torch tensor (contiguous), or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def version():
+    return lib().igp_version().decode()
+
+
+def launch_count():
+    return int(lib().igp_launch_count())
+
+
+def embed_opts(alpha=1.0, theta=0.1, eps=1e-3, x_scale=0.0, znorm_ddof=1, storage="f32", out_row_l2=False,
+               x_in=None, profile=None):
+    o = EmbedOpts()
+    lib().igp_embed_opts_init(ctypes.byref(o))
+    o.alpha, o.theta, o.eps, o.x_scale = alpha, theta, eps, x_scale
+    o.znorm_ddof = znorm_ddof
+    o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    o.out_row_l2 = 1 if out_row_l2 else 0
+    o.x_in = _ptr(x_in)
+    o.profile = profile.handle if profile is not None else None
+    return o
+
+
+class Profile:
+    """Per-phase device time recorded with CUDA events (igp_profile_*)."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(lib().igp_profile_create(ctypes.byref(h)))
+        self.handle = h.value
+
+    def read(self):
+        ms = (ctypes.c_double * IGP_NUM_PHASES)()
+        n = (ctypes.c_int64 * IGP_NUM_PHASES)()
+        _check(lib().igp_profile_read(self.handle, ms, n))
+        return {PHASE_NAMES[i]: (ms[i], n[i]) for i in range(IGP_NUM_PHASES)}
+
+    def close(self):
+        if self.handle:
+            lib().igp_profile_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    """Owning wrapper of an igp_graph handle."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def info(self):
+        n = ctypes.c_int32()
+        nnz = ctypes.c_int64()
+        md = ctypes.c_int32()
+        _check(lib().igp_graph_info(self.handle, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(md)))
+        return n.value, nnz.value, md.value
+
+    @property
+    def N(self):
+        return self.info()[0]
+
+    @property
+    def nnz(self):
+        return self.info()[1]
+
+    def export(self, row_ptr=None, col=None, stream=None):
+        """Copy the CSR into the given buffers, or into new numpy arrays if none given."""
+        N, nnz, _ = self.info()
+        if row_ptr is None and col is None:
+            row_ptr = np.empty(N + 1, dtype=np.int32)
+            col = np.empty(nnz, dtype=np.int32)
+        _check(lib().igp_graph_export(self.handle, _ptr(row_ptr), _ptr(col), _stream(stream)))
+        return row_ptr, col
+
+    def free(self):
+        if self.handle:
+            lib().igp_graph_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def graph_build(src, dst, N, stream=None, profile=None):
+    """igp_graph_build: src/dst int32 (numpy or torch, host or device)."""
+    M = int(src.shape[0])
+    if int(dst.shape[0]) != M:
+        raise ValueError("src and dst differ in length")
+    for a in (src, dst):
+        if str(a.dtype) not in ("int32", "torch.int32"):
+            raise TypeError("edge arrays must be int32")
+    h = ctypes.c_void_p()
+    if profile is None:
+        st = lib().igp_graph_build(_ptr(src), _ptr(dst), M, int(N), _stream(stream), ctypes.byref(h))
+    else:
+        st = lib().igp_graph_build_profiled(_ptr(src), _ptr(dst), M, int(N), _stream(stream), profile.handle,
+                                            ctypes.byref(h))
+    _check(st)
+    return Graph(h.value)
+
+
+def degree_factors(g, tau, eps=1e-3, out=None, stream=None):
+    """igp_degree_factors: fp32 D_tau^{-1/2} (numpy array unless `out` is given)."""
+    if out is None:
+        out = np.empty(g.N, dtype=np.float32)
+    _check(lib().igp_degree_factors(g.handle, float(tau), float(eps), _ptr(out), _stream(stream)))
+    return out
+
+
+def generate_x(seed, N, d, x_scale=0.0, out=None, stream=None):
+    """igp_generate_x: the Theta igp_embed draws, as fp32 [N, d]."""
+    if out is None:
+        out = np.empty((N, d), dtype=np.float32)
+    _check(lib().igp_generate_x(int(seed) & 0xFFFFFFFFFFFFFFFF, int(N), int(d), float(x_scale), _ptr(out),
+                                _stream(stream)))
+    return out
+
+
+def embed(g, tau, L, d, seed, out=None, opts=None, stream=None, **kw):
+    """igp_embed: one FFP; returns `out` (a new numpy array if not given)."""
+    if opts is None:
+        opts = embed_opts(**kw)
+    elif kw:
+        raise ValueError("give either opts or keyword options")
+    if out is None:
+        out = np.empty((g.N, d), dtype=np.float32)
+    _check(lib().igp_embed(g.handle, float(tau), int(L), int(d), int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out),
+                           ctypes.byref(opts), _stream(stream)))
+    return out

@@ -1,0 +1,99 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <vector>
+
+#include "igp.h"
+
+namespace igp {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+void clear_error();
+igp_status cuda_status(cudaError_t e, const char* what, const char* file, int line);
+
+#define IGP_TRY_CUDA(expr)                                                          \
+  do {                                                                              \
+    cudaError_t _e = (expr);                                                        \
+    if (_e != cudaSuccess) return ::igp::cuda_status(_e, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+#define IGP_TRY(expr)                  \
+  do {                                 \
+    igp_status _s = (expr);            \
+    if (_s != IGP_OK) return _s;       \
+  } while (0)
+
+// Count one kernel launch and surface launch-configuration errors.
+igp_status after_launch(const char* name);
+
+// ---------------------------------------------------------------- memory
+// Stream-ordered allocation from a library-private pool that keeps freed memory
+// cached (release threshold = max), so per-call workspaces cost no driver calls
+// after warm-up.
+igp_status dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+bool is_device_ptr(const void* p);
+int num_sms();
+
+// ---------------------------------------------------------------- profile
+struct Profile {
+  struct Rec {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get();
+};
+// Records an event pair around a phase when p != nullptr.
+struct PhaseTimer {
+  Profile* p;
+  int phase;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  PhaseTimer(Profile* p_, int ph, cudaStream_t s_);
+  ~PhaseTimer();
+};
+
+}  // namespace igp
+
+struct igp_profile {
+  igp::Profile prof;
+};
+
+struct igp_graph {
+  int32_t N = 0;
+  int64_t nnz = 0;
+  int32_t max_deg = 0;
+  int device = 0;
+  int32_t* row_ptr = nullptr;  // device [N+1]
+  int32_t* col = nullptr;      // device [nnz]
+  // Eq. 1 factors for the last (tau, eps) asked for
+  float* dinv = nullptr;       // device [N]
+  double dinv_tau = 0, dinv_eps = 0;
+  bool dinv_valid = false;
+  // FFP workspace (grown on demand, kept until free)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  // recorded on the stream of each call: later calls on another stream, and the
+  // stream-ordered release in igp_graph_free, wait for it
+  cudaEvent_t done = nullptr;
+};
+
+namespace igp {
+// csr_build.cu: CSR of the undirected edge list (device inputs), into g (empty).
+igp_status build_csr(const int32_t* src, const int32_t* dst, int64_t M, int32_t N, cudaStream_t s,
+                     igp_graph* g);
+// ffp.cu
+igp_status compute_dinv(igp_graph* g, double tau, double eps, cudaStream_t s, Profile* prof);
+igp_status launch_theta(uint64_t seed, int32_t N, int32_t d, float x_scale, int storage, void* out,
+                        cudaStream_t s);
+igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed, float* out_dev,
+                   const igp_embed_opts& o, cudaStream_t s);
+}  // namespace igp

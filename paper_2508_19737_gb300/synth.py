@@ -226,3 +226,26 @@ def split_increments(graph, T=10, mode="random", seed=0):
         m = step == t
         out.append((su[m].astype(np.int32), sv[m].astype(np.int32), int(bounds[t + 1])))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Named workloads (graph recipe + FFP settings). tau, L, d follow the paper's
+# settings where it fixes them (Table II gives tau < 0, L ~ 10, d in {16..64}).
+# ---------------------------------------------------------------------------
+WORKLOADS = {
+    # 1,000 nodes, 11 equal blocks, mean degree 20, gamma 2.5, per-pair ratio 10
+    "dcsbm-1k": dict(graph=dict(N=1000, B=11, mean_deg=20, gamma=2.5, ratio=10, seed=0),
+                     d=32, tau=-0.5, L=10, storage="f32"),
+    # 200,000 nodes, 64 Dirichlet(2) blocks, mean degree 25, gamma 2.5, ratio 4
+    "dcsbm-200k": dict(graph=dict(N=200_000, B=64, mean_deg=25, gamma=2.5, ratio=4, seed=0, dirichlet_alpha=2.0),
+                       d=64, tau=-0.5, L=10, storage="f32"),
+    # 2,000,000 nodes, 128 Dirichlet(5) blocks, mean degree 40, gamma 2.2, ratio 6,
+    # node ids ordered block-major then by decreasing degree
+    "dcsbm-2m": dict(graph=dict(N=2_000_000, B=128, mean_deg=40, gamma=2.2, ratio=6, seed=0, dirichlet_alpha=5.0,
+                                order="block_degree"),
+                     d=64, tau=-0.5, L=10, storage="bf16"),
+}
+
+
+def workload_graph(name):
+    return dcsbm(**WORKLOADS[name]["graph"])

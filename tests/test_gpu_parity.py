@@ -1,0 +1,266 @@
+"""CUDA path (through the C-ABI) against the FP64 oracle on the same seeded inputs.
+
+Bars: CSR, degrees and the fp32 degree factors bit-exact; Theta within a few
+fp32 ulps; embeddings within 1e-4 max per-row relative L2 error for fp32
+storage and 2e-2 for bf16 storage (max over rows of ||z_gpu - z_ref|| / ||z_ref||).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2508_19737_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-4, "bf16": 2e-2}
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_19737_gb300 import api as a
+    torch.cuda.set_device(0)
+    return a
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def row_rel_err(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.max(np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+
+
+def _random_multigraph(seed, N, M, loops=True):
+    rng = np.random.default_rng(seed)
+    src = rng.integers(0, N, M).astype(np.int32)
+    dst = rng.integers(0, N, M).astype(np.int32)
+    if loops and M:
+        k = rng.integers(0, M, max(1, M // 50))
+        dst[k] = src[k]
+    rep = rng.integers(0, M, M // 10) if M else np.zeros(0, dtype=np.int64)
+    return np.concatenate([src, dst[rep]]), np.concatenate([dst, src[rep]])  # some reversed repeats
+
+
+# ---------------------------------------------------------------------------- CSR + Eq. 1
+CSR_CASES = {
+    "dcsbm-1k": lambda: (lambda g: (g.src, g.dst, g.N))(synth.dcsbm(1000, 11, 20, 2.5, 10, seed=0)),
+    "multigraph": lambda: (*_random_multigraph(1, 5003, 40000), 5003),
+    "single-node": lambda: (np.zeros(3, np.int32), np.zeros(3, np.int32), 1),
+    "no-edges": lambda: (np.zeros(0, np.int32), np.zeros(0, np.int32), 77),
+    "hub-rows": lambda: (  # rows longer than a warp's sort capacity and than shared memory
+        np.concatenate([np.zeros(60000, np.int32), np.full(3000, 7, np.int32), np.arange(1, 5000, dtype=np.int32)]),
+        np.concatenate([np.random.default_rng(2).integers(1, 70000, 60000).astype(np.int32),
+                        np.random.default_rng(3).integers(0, 70000, 3000).astype(np.int32),
+                        np.arange(2, 5001, dtype=np.int32)]), 70000),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CSR_CASES))
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_csr_bit_exact(api, case, where):
+    src, dst, N = CSR_CASES[case]()
+    rp_ref, col_ref = oracle.build_csr(src, dst, N)
+    s, d = (src, dst) if where == "host" else (_dev(src), _dev(dst))
+    g = api.graph_build(s, d, N)
+    n, nnz, maxdeg = g.info()
+    rp, col = g.export()
+    assert n == N and nnz == col_ref.size
+    assert np.array_equal(rp, rp_ref) and np.array_equal(col, col_ref)
+    assert maxdeg == (int(np.diff(rp_ref).max()) if N else 0)
+    g.free()
+
+
+def test_csr_rejects_out_of_range_ids(api):
+    with pytest.raises(api.IgpError) as e:
+        api.graph_build(np.array([0, 1, 2], np.int32), np.array([1, 9, 0], np.int32), 5)
+    assert e.value.status == api.IGP_E_INVAL and "edge 1" in str(e.value)
+    with pytest.raises(api.IgpError):
+        api.graph_build(np.array([-1], np.int32), np.array([0], np.int32), 5)
+
+
+@pytest.mark.parametrize("tau", [-0.5, -1.5, -6.0, -80.0, 0.0, 3.0])
+def test_degree_factors_bit_exact(api, tau):
+    src, dst, N = CSR_CASES["multigraph"]()
+    src = np.concatenate([src, np.array([N - 1], np.int32)])  # plus an isolated node below
+    dst = np.concatenate([dst, np.array([N - 1], np.int32)])
+    g = api.graph_build(src, dst, N + 1)
+    rp, _ = oracle.build_csr(src, dst, N + 1)
+    ref = oracle.inv_sqrt_degrees(oracle.degree_correction(oracle.degrees(rp), tau)).astype(np.float32)
+    got = api.degree_factors(g, tau)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    g.free()
+
+
+# ---------------------------------------------------------------------------- Theta
+@pytest.mark.parametrize("N,d,seed", [(1000, 32, 0), (4099, 64, 12345), (17, 8, 2**63 + 5), (300, 128, 7)])
+def test_theta_matches_oracle(api, N, d, seed):
+    got = api.generate_x(seed, N, d).astype(np.float64)
+    ref = oracle.theta_input(seed, N, d)
+    xs = 1.0 / math.sqrt(d)
+    np.testing.assert_allclose(got, ref, rtol=2e-6, atol=1e-6 * xs)
+    # device output equals host output bit for bit
+    import torch
+    dev = torch.empty((N, d), dtype=torch.float32, device="cuda")
+    api.generate_x(seed, N, d, out=dev)
+    assert np.array_equal(dev.cpu().numpy(), got.astype(np.float32))
+
+
+# ---------------------------------------------------------------------------- FFP
+def _ffp_case(api, src, dst, N, d, tau, L, storage="f32", seed=0, device_out=True, **kw):
+    import torch
+    g = api.graph_build(_dev(src), _dev(dst), N)
+    if device_out:
+        out = torch.empty((N, d), dtype=torch.float32, device="cuda")
+        api.embed(g, tau, L, d, seed, out=out, storage=storage, **kw)
+        got = out.cpu().numpy()
+    else:
+        got = api.embed(g, tau, L, d, seed, storage=storage, **kw)
+    g.free()
+    rp, col = oracle.build_csr(src, dst, N)
+    okw = {k: v for k, v in kw.items() if k in ("alpha", "theta", "eps", "out_row_l2")}
+    if "znorm_ddof" in kw:
+        okw["ddof"] = kw["znorm_ddof"]
+    X = oracle.theta_input(seed, N, d, x_scale=kw.get("x_scale") or None)
+    ref = oracle.ffp(rp, col, X, tau, L, **okw)
+    return got, ref, (rp, col, X, okw)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_small_config_parity(api, storage):
+    g = synth.dcsbm(1000, 11, 20, 2.5, 10, seed=0)
+    got, ref, _ = _ffp_case(api, g.src, g.dst, g.N, 32, -0.5, 10, storage=storage)
+    assert row_rel_err(got, ref) <= TOL[storage]
+
+
+@pytest.mark.parametrize("d", [8, 16, 32, 64, 128])
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_every_width_parity(api, d, storage):
+    # ragged sizes: N not a multiple of any tile, rows from degree 0 to a few hundred
+    g = synth.dcsbm(4099, 13, 18, 2.5, 5, seed=d)
+    got, ref, _ = _ffp_case(api, g.src, g.dst, g.N, d, -0.5, 6, storage=storage, seed=d + 1)
+    assert row_rel_err(got, ref) <= TOL[storage]
+
+
+@pytest.mark.parametrize("opts", [
+    dict(znorm_ddof=0),
+    dict(out_row_l2=True),
+    dict(alpha=-0.5, theta=0.7),          # high-pass filter (Eq. 2, alpha < 0)
+    dict(x_scale=1.0),                    # Theta ~ N(0, 1)
+    dict(eps=1e-2),
+])
+def test_option_parity(api, opts):
+    g = synth.dcsbm(3001, 9, 16, 2.5, 6, seed=4)
+    got, ref, _ = _ffp_case(api, g.src, g.dst, g.N, 32, -1.0, 5, **opts)
+    assert row_rel_err(got, ref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("tau,L", [(0.0, 4), (3.0, 4), (-6.0, 10), (-80.0, 5), (-0.5, 0), (-0.5, 1)])
+def test_tau_and_depth_parity(api, tau, L):
+    g = synth.dcsbm(2500, 7, 30, 2.5, 6, seed=5)
+    got, ref, _ = _ffp_case(api, g.src, g.dst, g.N, 32, tau, L)
+    assert row_rel_err(got, ref) <= TOL["f32"]
+
+
+def test_degenerate_graphs(api):
+    # edgeless graph (Ahat = 0), a single node (std of one value -> column 0), isolated nodes
+    got, ref, _ = _ffp_case(api, np.zeros(0, np.int32), np.zeros(0, np.int32), 50, 16, -0.5, 3)
+    assert row_rel_err(got, ref) <= TOL["f32"]
+    got, ref, _ = _ffp_case(api, np.zeros(0, np.int32), np.zeros(0, np.int32), 1, 16, -0.5, 3)
+    assert np.array_equal(got, np.full((1, 16), 0.5, np.float32)) and np.allclose(ref, 0.5)
+    src = np.array([0, 1, 5], np.int32)
+    dst = np.array([1, 2, 6], np.int32)
+    got, ref, _ = _ffp_case(api, src, dst, 40, 8, -1.5, 4)
+    assert row_rel_err(got, ref) <= TOL["f32"]
+
+
+def test_host_output_and_x_in(api):
+    import torch
+    g = synth.dcsbm(2000, 5, 12, 2.5, 5, seed=6)
+    got, ref, (rp, col, X, _) = _ffp_case(api, g.src, g.dst, g.N, 32, -0.5, 5, device_out=False)
+    assert row_rel_err(got, ref) <= TOL["f32"]
+    # a caller-supplied Z^(0)
+    Xc = np.random.default_rng(0).standard_normal((g.N, 32)).astype(np.float32)
+    gr = api.graph_build(g.src, g.dst, g.N)
+    out = api.embed(gr, -0.5, 5, 32, 0, x_in=torch.from_numpy(Xc).cuda())
+    gr.free()
+    assert row_rel_err(out, oracle.ffp(rp, col, Xc.astype(np.float64), -0.5, 5)) <= TOL["f32"]
+
+
+def test_bf16_against_bf16_emulating_oracle(api):
+    g = synth.dcsbm(20011, 32, 25, 2.5, 4, seed=7, dirichlet_alpha=2.0)
+    got, ref, (rp, col, X, _) = _ffp_case(api, g.src, g.dst, g.N, 64, -0.5, 10, storage="bf16")
+    e64 = row_rel_err(got, ref)
+    emu = oracle.ffp(rp, col, X, -0.5, 10, storage="bf16")
+    e_emu = row_rel_err(got, emu)
+    assert e64 <= TOL["bf16"]
+    assert e_emu <= e64  # the storage-rounding model explains most of the difference
+
+
+def test_deterministic_and_stream_ordered(api):
+    import torch
+    g = synth.dcsbm(30000, 20, 25, 2.5, 4, seed=8)
+    gr = api.graph_build(_dev(g.src), _dev(g.dst), g.N)
+    s = torch.cuda.Stream()
+    outs = []
+    for _ in range(2):
+        o = torch.empty((g.N, 64), dtype=torch.float32, device="cuda")
+        with torch.cuda.stream(s):
+            api.embed(gr, -0.5, 10, 64, 3, out=o, storage="bf16", stream=s)
+        s.synchronize()
+        outs.append(o.cpu().numpy())
+    gr.free()
+    assert np.array_equal(outs[0], outs[1])
+
+
+# ---------------------------------------------------------------------------- workloads
+def test_200k_config_parity_both_storages(api):
+    wl = synth.WORKLOADS["dcsbm-200k"]
+    g = synth.workload_graph("dcsbm-200k")
+    import torch
+    gr = api.graph_build(_dev(g.src), _dev(g.dst), g.N)
+    rp, col = oracle.build_csr(g.src, g.dst, g.N)
+    X = oracle.theta_input(0, g.N, wl["d"])
+    ref = oracle.ffp(rp, col, X, wl["tau"], wl["L"])
+    for storage in ("f32", "bf16"):
+        out = torch.empty((g.N, wl["d"]), dtype=torch.float32, device="cuda")
+        api.embed(gr, wl["tau"], wl["L"], wl["d"], 0, out=out, storage=storage)
+        assert row_rel_err(out.cpu().numpy(), ref) <= TOL[storage]
+    gr.free()
+
+
+def test_2m_config_full_size(api):
+    """The 2M-node workload in the configuration the benchmark times: bit-exact CSR and
+    degree factors, one and two full layers against the oracle, and properties of the
+    full 10-layer output (logits have column mean 0 and sample std 1)."""
+    import torch
+    wl = synth.WORKLOADS["dcsbm-2m"]
+    g = synth.workload_graph("dcsbm-2m")
+    gr = api.graph_build(_dev(g.src), _dev(g.dst), g.N)
+    rp, col = oracle.build_csr(g.src, g.dst, g.N)
+    rpg, colg = gr.export()
+    assert np.array_equal(rpg, rp) and np.array_equal(colg, col)
+    del colg
+    ref_dinv = oracle.inv_sqrt_degrees(oracle.degree_correction(oracle.degrees(rp), wl["tau"])).astype(np.float32)
+    assert np.array_equal(api.degree_factors(gr, wl["tau"]).view(np.uint32), ref_dinv.view(np.uint32))
+    d = wl["d"]
+    X = oracle.theta_input(0, g.N, d)
+    out = torch.empty((g.N, d), dtype=torch.float32, device="cuda")
+    for L in (1, 2):
+        ref = oracle.ffp(rp, col, X, wl["tau"], L)
+        api.embed(gr, wl["tau"], L, d, 0, out=out, storage=wl["storage"])
+        assert row_rel_err(out.cpu().numpy(), ref) <= TOL[wl["storage"]]
+    api.embed(gr, wl["tau"], wl["L"], d, 0, out=out, storage=wl["storage"])
+    z = out.double()
+    z = torch.log(z) - torch.log1p(-z)
+    assert torch.isfinite(z).all()
+    assert float(z.mean(0).abs().max()) < 1e-2
+    assert float((z.std(0) - 1).abs().max()) < 2e-2
+    gr.free()
