@@ -74,7 +74,10 @@ typedef struct igp_embed_opts {
   int32_t znorm_ddof;  /* ZNorm standard deviation divisor N - ddof; 1 (0 allowed) */
   int32_t storage;     /* IGP_STORE_F32 (default) or IGP_STORE_BF16 */
   int32_t out_row_l2;  /* 1: divide each output row by its L2 norm; 0 (default) */
-  int32_t reserved0;
+  int32_t chunk_cols;  /* columns per layer pass; 0 (default) picks the widest of d, d/2, d/4, ..
+                          whose N x width slice of the activations fits ~72 MB of L2, keeping at
+                          least 128 bytes per row. Otherwise a power of two dividing d, >= 8, with
+                          at least 16 bytes per row. Result-neutral (exact integer statistics). */
   const void* x_in;    /* NULL: Theta from `seed`. Else a DEVICE pointer to N x d row-major values in
                           the storage type, used as Z^(0) instead (not modified). */
   igp_profile* profile;/* NULL, or a profile that records per-phase device times of this call */

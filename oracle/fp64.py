@@ -152,10 +152,11 @@ def ffp(row_ptr, col, X, tau, L, alpha=1.0, theta=0.1, eps=1e-3, ddof=1,
         out_row_l2=False, storage="f64", return_layers=False):
     """One FFP over the graph given in CSR form, on the input X = Theta.
 
-    storage="bf16" rounds to BF16 at the points where the GPU stores in BF16
-    (Theta, and each layer's tanh output T^(l)); the column statistics of a
-    layer are those of its unrounded T^(l). It only separates storage error from
-    bugs; the fp64 result is the contract.
+    storage="bf16" rounds to BF16 where the GPU stores in BF16: Theta and each
+    layer's tanh output T^(l) are stored row-scaled, as dinv_i * x_i (x_i where
+    dinv_i = 0), so the rounding is applied to that product and undone by the
+    division; the column statistics of a layer are those of its unrounded T^(l).
+    It only separates storage error from bugs; the fp64 result is the contract.
     Returns Z~ (N x d, fp64), plus per-layer (T, mean, std) if asked.
     """
     row_ptr = np.asarray(row_ptr, dtype=np.int64)
@@ -163,10 +164,14 @@ def ffp(row_ptr, col, X, tau, L, alpha=1.0, theta=0.1, eps=1e-3, ddof=1,
     X = np.asarray(X, dtype=np.float64)
     if X.shape[0] != N:
         raise ValueError("X must have N rows")
-    store = round_bf16 if storage == "bf16" else (lambda a: a)
     # line 1: D_tau via Eq. 1, and the normalised adjacency of Eq. 3
     dinv = inv_sqrt_degrees(degree_correction(degrees(row_ptr), tau, eps))
     Ahat = normalized_adjacency(row_ptr, col, dinv)
+    if storage == "bf16":
+        sc = np.where(dinv > 0, dinv, 1.0)[:, None]
+        store = lambda a: round_bf16(sc * a) / sc  # noqa: E731
+    else:
+        store = lambda a: a  # noqa: E731
     # lines 2-3: Z^(0) = Theta
     Z = store(X)
     layers = []

@@ -296,6 +296,7 @@ void igp_graph_free(igp_graph* g) {
   if (g->row_ptr) cudaFreeAsync(g->row_ptr, s);
   if (g->col) cudaFreeAsync(g->col, s);
   if (g->dinv) cudaFreeAsync(g->dinv, s);
+  if (g->perm) cudaFreeAsync(g->perm, s);
   if (g->ws) cudaFreeAsync(g->ws, s);
   if (g->done) cudaEventDestroy(g->done);
   cudaGetLastError();
@@ -312,10 +313,10 @@ igp_status igp_generate_x(uint64_t seed, int32_t N, int32_t d, double x_scale, f
   cudaStream_t s = (cudaStream_t)stream;
   const double xs = x_scale > 0 ? x_scale : 1.0 / std::sqrt((double)d);
   const size_t bytes = (size_t)N * d * sizeof(float);
-  if (is_device_ptr(out)) return launch_theta(seed, N, d, (float)xs, IGP_STORE_F32, out, s);
+  if (is_device_ptr(out)) return launch_theta(seed, N, d, d, (float)xs, IGP_STORE_F32, nullptr, out, s);
   void* tmp = nullptr;
   IGP_TRY(dev_alloc(&tmp, bytes, s));
-  igp_status st = launch_theta(seed, N, d, (float)xs, IGP_STORE_F32, tmp, s);
+  igp_status st = launch_theta(seed, N, d, d, (float)xs, IGP_STORE_F32, nullptr, tmp, s);
   if (st == IGP_OK) st = copy_out(out, tmp, bytes, s);
   dev_free(tmp, s);
   return st;
@@ -342,6 +343,14 @@ igp_status igp_embed(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t se
   if (d != 8 && d != 16 && d != 32 && d != 64 && d != 128) {
     set_error("igp_embed: d=%d unsupported (8, 16, 32, 64, 128)", d);
     return IGP_E_INVAL;
+  }
+  if (o.chunk_cols != 0) {
+    const int sb = o.storage == IGP_STORE_BF16 ? 2 : 4;
+    const int c = o.chunk_cols;
+    if (c < 0 || c > d || d % c != 0 || (c & (c - 1)) != 0 || c * sb < 16) {
+      set_error("igp_embed: chunk_cols=%d must be a power of two dividing d=%d with >= 16 bytes per row", c, d);
+      return IGP_E_INVAL;
+    }
   }
   if (o.x_in && !is_device_ptr(o.x_in)) {
     set_error("igp_embed: opts->x_in must be device memory");

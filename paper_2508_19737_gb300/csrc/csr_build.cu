@@ -131,6 +131,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int* __restri
   }
 }
 
+}  // namespace
+
 // Exclusive scan of n ints (n >= 1). tmp must hold ceil(n / kScanTile) ints.
 igp_status exclusive_scan(const int* in, int* out, int64_t n, int* tmp, cudaStream_t s) {
   int64_t ntiles = (n + kScanTile - 1) / kScanTile;
@@ -141,6 +143,8 @@ igp_status exclusive_scan(const int* in, int* out, int64_t n, int* tmp, cudaStre
   k_scan_tiles<<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, tmp, out);
   return after_launch("k_scan_tiles");
 }
+
+namespace {
 
 // ------------------------------------------------------------------ count / scatter
 __global__ void k_count(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t M,

@@ -1,25 +1,33 @@
 // The feed-forward propagation (FFP) of InfraredGP, Alg. 1 lines 1-6:
-//   k_dinv    Eq. 1 degree correction D_tau and D_tau^{-1/2} (fp64, rounded to fp32)
-//   k_theta   Z^(0) = Theta ~ N(0, 1/d): Philox4x64-10 + Box-Muller (Alg. 1, line 2)
-//   k_layer   one Eq. 4 layer: T^(l) = tanh(theta Z + alpha Ahat Z), Z = ZNorm(T^(l-1)),
-//             fused with the column statistics of T^(l) that the next ZNorm needs
-//   k_output  Z~ = sigmoid(ZNorm(T^(L))) (Eq. 4), optional row L2 normalisation
+//   k_dinv        Eq. 1 degree correction D_tau and D_tau^{-1/2} (fp64, rounded to fp32)
+//   k_wsum        w_i = sum_{j in N(i)} dinv_j (fp32), once per graph and tau
+//   k_deg_*       rows in order of decreasing degree, once per graph
+//   k_theta       Z^(0) = Theta ~ N(0, 1/d): Philox4x64-10 + Box-Muller (Alg. 1, line 2)
+//   k_layer       one Eq. 4 layer: T^(l) = tanh(theta Z + alpha Ahat Z), Z = ZNorm(T^(l-1)),
+//                 fused with the column statistics of T^(l) that the next ZNorm needs
+//   k_output      Z~ = sigmoid(ZNorm(T^(L))) (Eq. 4), optional row L2 normalisation
 //
-// Layer kernel design (bandwidth-bound sparse gather, no tensor cores):
-//   * one warp per row; its 32 lanes are NS neighbour slots x G column chunks, a chunk
-//     being 16 bytes of the stored row (8 bf16 or 4 fp32 values), so a neighbour row
-//     is fetched by G lanes with one 16-byte load each;
-//   * slot s takes neighbours beg+s, beg+s+NS, ...; U neighbours per slot are in
-//     flight per iteration and the next iteration's column indices are prefetched;
-//   * ZNorm of the input is applied after the gather, per row:
-//       sum_j dinv_j z_j = inv_s (sum_j dinv_j t_j - mu sum_j dinv_j),
-//     so a neighbour costs one FMA per element;
-//   * the NS slot partial sums are combined by a shuffle reduce-scatter, after which
-//     each lane owns EPL columns of the row and applies the epilogue (self term,
-//     tanh, store, running column sums) to them only;
-//   * column statistics: per-lane fp32 sums of t and t^2, a fixed-order CTA
-//     reduction to one partial per CTA, and the last CTA to finish (ticket counter)
-//     reduces the partials in fixed order and forms mean and 1/std in fp64.
+// Storage: row i of every N x d activation buffer holds s_i = dinv_i * t_i (t_i itself
+// when dinv_i = 0, an isolated node at tau = 0). With Z = ZNorm(T) = (T - mu) inv_s,
+//     sum_j dinv_j z_j = inv_s (sum_j s_j - mu w_i),
+// so a layer gathers neighbour rows and only adds them: no per-neighbour degree
+// factor, no per-neighbour normalisation; the self term uses t_i = s_i / dinv_i.
+//
+// Layer kernel (bandwidth-bound sparse gather, no tensor cores):
+//   * a group of G lanes owns one row; each lane owns 16 bytes of it (8 bf16 or 4 fp32
+//     values), so a neighbour row is G coalesced 16-byte loads;
+//   * rows are visited in decreasing-degree order in warp tiles of 32/G rows, so the
+//     groups of a warp have (nearly) the same trip count and stay converged;
+//   * kChunk neighbour rows per group are in flight per trip; the next trip's column
+//     indices and the next tile's rows (perm entry, row bounds, self row, dinv, w) are
+//     prefetched while the current trip is gathered;
+//   * wide rows are split into column chunks (blockIdx.y) so that the gathered slice of
+//     T^(l-1) stays L2-resident; column indices are loaded with an evict-first policy
+//     and outputs are stored streaming;
+//   * epilogue per row: self term, tanh, store s_i, and exact integer column sums of t
+//     and t^2 (fixed point 2^-30); a warp/CTA reduction gives one partial per CTA and
+//     the last CTA to finish (ticket counter) adds them up and forms mean and 1/std
+//     in fp64. Integer sums make the result independent of the row order.
 #include <cmath>
 #include <cstdio>
 
@@ -124,6 +132,34 @@ __device__ __forceinline__ void store_small(__nv_bfloat16* p, const float (&v)[E
 
 constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
 
+// Activation layout: column blocks of dc columns, each block an N x dc row-major array
+// (dc = d: plain row-major). Offset of element (i, c).
+__device__ __forceinline__ int64_t blk_off(int64_t i, int c, int32_t N, int dc) {
+  const int q = c / dc;
+  return (int64_t)q * N * dc + i * dc + (c - q * dc);
+}
+
+// Streamed-once data (column indices): keep it out of L1 and first in line for L2 eviction,
+// so it does not push the gathered rows out of L2.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ int ld_stream(const int* p, uint64_t pol) {
+  int v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+// Rows written by a layer are read again only by the next layer: streaming stores.
+__device__ __forceinline__ void store_chunk_cs(float* p, const float (&v)[4]) {
+  __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+}
+__device__ __forceinline__ void store_chunk_cs(__nv_bfloat16* p, const float (&v)[8]) {
+  __stcs(reinterpret_cast<uint4*>(p), make_uint4(bf_pack(v[0], v[1]), bf_pack(v[2], v[3]), bf_pack(v[4], v[5]),
+                                                 bf_pack(v[6], v[7])));
+}
+
 // ------------------------------------------------------------------ Eq. 1
 __global__ void k_dinv(const int32_t* __restrict__ row_ptr, int32_t N, double tau, double eps,
                        float* __restrict__ dinv) {
@@ -182,8 +218,10 @@ __device__ __forceinline__ void theta8(uint64_t seed, uint64_t i, uint64_t q, fl
   }
 }
 
+// Theta, stored as dinv_i * Theta_i when dinv is given (the layer storage convention).
 template <typename S>
-__global__ void k_theta(uint64_t seed, int32_t N, int32_t d, float xs, S* __restrict__ out) {
+__global__ void k_theta(uint64_t seed, int32_t N, int32_t d, int32_t dc, float xs, const float* __restrict__ dinv,
+                        S* __restrict__ out) {
   const int nq = d >> 3;
   const int64_t total = (int64_t)N * nq;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -191,7 +229,14 @@ __global__ void k_theta(uint64_t seed, int32_t N, int32_t d, float xs, S* __rest
     const int q = (int)(t - i * nq);
     float z[8];
     theta8(seed, (uint64_t)i, (uint64_t)q, xs, z);
-    S* p = out + i * d + q * 8;
+    if (dinv) {
+      const float di = __ldg(dinv + i);
+      if (di > 0.0f) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) z[k] *= di;
+      }
+    }
+    S* p = out + blk_off(i, q * 8, N, dc);
     if constexpr (sizeof(S) == 2) {
       store_chunk(p, z);
     } else {
@@ -202,145 +247,304 @@ __global__ void k_theta(uint64_t seed, int32_t N, int32_t d, float xs, S* __rest
   }
 }
 
-// ------------------------------------------------------------------ Eq. 4 layer
-template <int D, typename S, int U>
-__global__ void __launch_bounds__(kLayerThreads) k_layer(
-    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const float* __restrict__ dinv,
-    const S* __restrict__ Tin, S* __restrict__ Tout, const float* __restrict__ stats_in,
-    float* __restrict__ partials, float* __restrict__ stats_out, unsigned* __restrict__ ticket, int32_t N,
-    float alpha, float theta, int ddof) {
+// ------------------------------------------------------------------ per-graph helpers
+// w_i = sum_{j in N(i)} dinv_j, one warp per row, fixed order.
+__global__ void k_wsum(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                       const float* __restrict__ dinv, int32_t N, float* __restrict__ wsum) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < N;
+       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int b = row_ptr[i], e = row_ptr[i + 1];
+    float a = 0.0f;
+    for (int k = b + lane; k < e; k += 32) a += __ldg(dinv + __ldg(col + k));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) wsum[i] = a;
+  }
+}
+
+// Rows in order of decreasing degree (counting sort by key max_deg - deg: block-local
+// shared-memory histograms, a scan, one global atomic per block and key, then an atomic
+// scatter). The order among rows of equal degree is whatever the atomics give; nothing
+// computed from it depends on that order (each row's result, and the exact integer
+// column sums of the layer kernel).
+constexpr int kPermRowsPerBlock = 4096;
+constexpr int kPermSmemBins = 12 * 1024;  // keys handled in shared memory (48 KB)
+
+__device__ __forceinline__ int deg_key(const int32_t* row_ptr, int64_t i, int32_t max_deg) {
+  return max_deg - (row_ptr[i + 1] - row_ptr[i]);
+}
+
+__global__ void k_deg_hist(const int32_t* __restrict__ row_ptr, int32_t N, int32_t max_deg, int* __restrict__ hist) {
+  extern __shared__ int sh[];
+  const int nb = max_deg + 1;
+  const bool local = nb <= kPermSmemBins;
+  const int64_t i0 = (int64_t)blockIdx.x * kPermRowsPerBlock;
+  const int64_t i1 = min((int64_t)N, i0 + kPermRowsPerBlock);
+  if (local) {
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) sh[k] = 0;
+    __syncthreads();
+  }
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const int k = deg_key(row_ptr, i, max_deg);
+    atomicAdd(local ? &sh[k] : &hist[k], 1);
+  }
+  if (local) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < nb; k += blockDim.x)
+      if (sh[k]) atomicAdd(&hist[k], sh[k]);
+  }
+}
+
+__global__ void k_deg_scatter(const int32_t* __restrict__ row_ptr, int32_t N, int32_t max_deg,
+                              const int* __restrict__ off, int* __restrict__ cur, int32_t* __restrict__ perm) {
+  extern __shared__ int sh[];
+  const int nb = max_deg + 1;
+  const bool local = nb <= kPermSmemBins;
+  const int64_t i0 = (int64_t)blockIdx.x * kPermRowsPerBlock;
+  const int64_t i1 = min((int64_t)N, i0 + kPermRowsPerBlock);
+  if (!local) {
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const int k = deg_key(row_ptr, i, max_deg);
+      perm[off[k] + atomicAdd(&cur[k], 1)] = (int32_t)i;
+    }
+    return;
+  }
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) sh[k] = 0;
+  __syncthreads();
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) atomicAdd(&sh[deg_key(row_ptr, i, max_deg)], 1);
+  __syncthreads();
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    const int c = sh[k];
+    if (c) sh[k] = off[k] + atomicAdd(&cur[k], c);  // this block's slots for key k
+  }
+  __syncthreads();
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const int k = deg_key(row_ptr, i, max_deg);
+    perm[atomicAdd(&sh[k], 1)] = (int32_t)i;
+  }
+}
+
+// A caller-supplied Z^(0) in the storage type, copied into the row-scaled storage.
+template <typename S>
+__global__ void k_prescale(const S* __restrict__ x, const float* __restrict__ dinv, int32_t N, int32_t d,
+                           int32_t dc, S* __restrict__ out) {
   constexpr int VPL = Store<S>::VPL;
-  constexpr int G = D / VPL;   // lanes per row copy (16 B each)
-  constexpr int NS = 32 / G;   // neighbour slots per warp
-  constexpr int EPL = VPL >= NS ? VPL / NS : 1;  // epilogue values per lane
-  constexpr int RS = ilog2(VPL / EPL);           // reduce-scatter steps
-  constexpr int AR = ilog2(NS) - RS;             // remaining all-reduce steps
-  static_assert(G >= 1 && G <= 32 && NS * G == 32, "unsupported width");
+  const int nc = d / VPL;
+  const int64_t total = (int64_t)N * nc;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / nc;
+    const int c = (int)(t - i * nc) * VPL;
+    float v[VPL];
+    load_chunk(x + t * VPL, v);
+    const float di = __ldg(dinv + i);
+    if (di > 0.0f) {
+#pragma unroll
+      for (int k = 0; k < VPL; ++k) v[k] *= di;
+    }
+    store_chunk(out + blk_off(i, c, N, dc), v);
+  }
+}
+
+// ------------------------------------------------------------------ Eq. 4 layer
+constexpr int kChunk = 8;  // neighbour rows in flight per row group per trip
+
+template <typename S>
+struct Raw;
+template <>
+struct Raw<float> {
+  using T = float4;
+  static __device__ __forceinline__ float4 load(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+  static __device__ __forceinline__ float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ void add(float (&a)[4], float4 x) {
+    a[0] += x.x; a[1] += x.y; a[2] += x.z; a[3] += x.w;
+  }
+  static __device__ __forceinline__ void unpack(float4 x, float (&v)[4]) {
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  }
+};
+template <>
+struct Raw<__nv_bfloat16> {
+  using T = uint4;
+  static __device__ __forceinline__ uint4 load(const __nv_bfloat16* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
+  static __device__ __forceinline__ uint4 zero() { return make_uint4(0u, 0u, 0u, 0u); }
+  static __device__ __forceinline__ void add(float (&a)[8], uint4 x) {
+    a[0] += bf_lo(x.x); a[1] += bf_hi(x.x); a[2] += bf_lo(x.y); a[3] += bf_hi(x.y);
+    a[4] += bf_lo(x.z); a[5] += bf_hi(x.z); a[6] += bf_lo(x.w); a[7] += bf_hi(x.w);
+  }
+  static __device__ __forceinline__ void unpack(uint4 x, float (&v)[8]) {
+    v[0] = bf_lo(x.x); v[1] = bf_hi(x.x); v[2] = bf_lo(x.y); v[3] = bf_hi(x.y);
+    v[4] = bf_lo(x.z); v[5] = bf_hi(x.z); v[6] = bf_lo(x.w); v[7] = bf_hi(x.w);
+  }
+};
+
+// Column sums of t and t^2 are accumulated as integers, t * 2^kQBits rounded to nearest
+// (|t| <= 1), so that they are exact and independent of the order rows are summed in.
+constexpr int kQBits = 30;
+constexpr float kQScale = 1073741824.0f;  // 2^30
+
+// Columns are processed in chunks of D (the template width) out of d per row:
+// blockIdx.y selects the chunk, whose N x D slice of T^(l-1) is one contiguous column
+// block of the activation layout and can stay in L2 while the chunk is processed.
+// Chunks are independent (tanh and the column statistics act per column); each has
+// its own partials and ticket.
+//
+// Rows are taken in `perm` order (decreasing degree) in tiles of GPW rows, one row per
+// group of G lanes; as the rows of a tile have (nearly) equal degree, the groups of a
+// warp run their gather loops in lockstep.
+template <int D, typename S>
+__global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const float* __restrict__ dinv,
+    const float* __restrict__ wsum, const int32_t* __restrict__ perm, const S* __restrict__ Tin_all,
+    S* __restrict__ Tout_all, const float* __restrict__ stats_in, long long* __restrict__ partials_all,
+    float* __restrict__ stats_out, unsigned* __restrict__ tickets, int32_t N, int32_t d, float alpha, float theta,
+    int ddof) {
+  using RW = Raw<S>;
+  using RT = typename RW::T;
+  constexpr int VPL = Store<S>::VPL;
+  constexpr int G = D / VPL;               // lanes per row
+  constexpr int GPW = 32 / G;              // rows per warp tile
+  constexpr int C = kChunk;                // neighbour rows per trip
+  constexpr int IPL = C >= G ? C / G : 1;  // trip indices held per lane
+  static_assert(G >= 1 && G <= 32 && GPW * G == 32, "unsupported width");
 
   __shared__ float s_mu[D], s_is[D];
-  __shared__ float s_red[kLayerWarps][2 * D];
+  __shared__ long long s_red[kLayerWarps][2 * D];
   __shared__ bool s_last;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int chunk = lane % G, slot = lane / G;
+  const int grp = lane / G, lig = lane % G;
+  const int c0 = blockIdx.y * D;  // first column of this chunk
+  const int64_t blk = (int64_t)blockIdx.y * N * D + lig * VPL;  // this lane's part of the column block
+  const S* __restrict__ Tin = Tin_all + blk;
+  S* __restrict__ Tout = Tout_all + blk;
+  long long* __restrict__ partials = partials_all + (int64_t)blockIdx.y * gridDim.x * 2 * D;
+  unsigned* ticket = tickets + blockIdx.y;
   for (int c = threadIdx.x; c < D; c += blockDim.x) {
-    s_mu[c] = stats_in ? stats_in[c] : 0.0f;
-    s_is[c] = stats_in ? stats_in[D + c] : 1.0f;
+    s_mu[c] = stats_in ? stats_in[c0 + c] : 0.0f;
+    s_is[c] = stats_in ? stats_in[d + c0 + c] : 1.0f;
   }
   __syncthreads();
+  const uint64_t pol = evict_first_policy();
 
-  // columns this lane owns after the reduce-scatter
-  int off = 0;
+  long long qs[VPL], qq[VPL];
 #pragma unroll
-  for (int b = 0; b < RS; ++b) {
-    const int sb = ilog2(NS) - 1 - b;
-    if ((slot >> sb) & 1) off += (VPL >> (b + 1));
-  }
-  const bool owner = AR == 0 || (slot & ((1 << AR) - 1)) == 0;
-  const int cc = chunk * VPL + off;
+  for (int v = 0; v < VPL; ++v) qs[v] = qq[v] = 0;
 
-  float mu_e[EPL], is_e[EPL];
-#pragma unroll
-  for (int e = 0; e < EPL; ++e) {
-    mu_e[e] = s_mu[cc + e];
-    is_e[e] = s_is[cc + e];
-  }
-  float csum[EPL], csq[EPL];
-#pragma unroll
-  for (int e = 0; e < EPL; ++e) csum[e] = csq[e] = 0.0f;
+  const int64_t ntiles = ((int64_t)N + GPW - 1) / GPW;
+  const int64_t nw = (int64_t)gridDim.x * kLayerWarps;
+  const int64_t w0 = (int64_t)blockIdx.x * kLayerWarps + warp;
 
-  const int64_t nwarps = (int64_t)gridDim.x * kLayerWarps;
-  for (int64_t i = (int64_t)blockIdx.x * kLayerWarps + warp; i < N; i += nwarps) {
-    const int beg = row_ptr[i], end = row_ptr[i + 1];
+  auto perm_at = [&](int64_t tile) -> int {
+    const int64_t p = tile * GPW + grp;
+    return (tile < ntiles && p < N) ? __ldg(perm + p) : -1;
+  };
+  // lane lig holds trip entries lig + G k (k < IPL) counted from `base`, below `end`
+  auto load_idx = [&](int (&jw)[IPL], int base, int end) {
+#pragma unroll
+    for (int k = 0; k < IPL; ++k) {
+      const int t = lig + G * k;
+      jw[k] = (t < C && base + t < end) ? ld_stream(col + base + t, pol) : 0;
+    }
+  };
+  struct RowData {
+    int b, e;
+    RT self;
+    float di, wi;
+  };
+  auto fetch_row = [&](int r, RowData& rd) {
+    if (r >= 0) {
+      rd.b = __ldg(row_ptr + r);
+      rd.e = __ldg(row_ptr + r + 1);
+      rd.self = RW::load(Tin + (int64_t)r * D);
+      rd.di = __ldg(dinv + r);
+      rd.wi = __ldg(wsum + r);
+    } else {
+      rd.b = rd.e = 0;
+      rd.self = RW::zero();
+      rd.di = rd.wi = 0.0f;
+    }
+  };
+
+  // three-stage pipeline over tiles: perm (t+2), row data (t+1), gathers (t)
+  int r = perm_at(w0);
+  RowData cur;
+  fetch_row(r, cur);
+  int r_n = perm_at(w0 + nw);
+  int jw[IPL];
+  load_idx(jw, cur.b, cur.e);
+  for (int64_t tile = w0; tile < ntiles; tile += nw) {
+    const int r_nn = perm_at(tile + 2 * nw);
+    RowData nxt;
+    fetch_row(r_n, nxt);
+
+    const int ntrip = (cur.e - cur.b + C - 1) / C;
+    const int mtrip = __reduce_max_sync(0xffffffffu, ntrip);
     float acc[VPL];
 #pragma unroll
     for (int v = 0; v < VPL; ++v) acc[v] = 0.0f;
-    float wsum = 0.0f;
-    // neighbours handled by this slot: beg + slot + NS * m
-    int k = beg + slot;
-    int jn[U];
+    for (int tr = 0; tr < mtrip; ++tr) {
+      const int c = cur.b + tr * C;
+      int jn[IPL];
+      load_idx(jn, c + C, cur.e);
+      RT x[C];
 #pragma unroll
-    for (int u = 0; u < U; ++u) jn[u] = (k + u * NS < end) ? __ldg(col + k + u * NS) : -1;
-    for (; k < end; k += U * NS) {
-      int j[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) j[u] = jn[u];
-      const int kn = k + U * NS;
-#pragma unroll
-      for (int u = 0; u < U; ++u) jn[u] = (kn + u * NS < end) ? __ldg(col + kn + u * NS) : -1;
-      float w[U];
-      float x[U][VPL];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (j[u] >= 0) {
-          w[u] = __ldg(dinv + j[u]);
-          load_chunk(Tin + (int64_t)j[u] * D + chunk * VPL, x[u]);
-        } else {
-          w[u] = 0.0f;
-#pragma unroll
-          for (int v = 0; v < VPL; ++v) x[u][v] = 0.0f;
-        }
+      for (int t = 0; t < C; ++t) {
+        const int j = __shfl_sync(0xffffffffu, jw[t / G], t % G, G);
+        x[t] = (c + t < cur.e) ? RW::load(Tin + (int64_t)j * D) : RW::zero();
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        wsum += w[u];
+      for (int t = 0; t < C; ++t) RW::add(acc, x[t]);
 #pragma unroll
-        for (int v = 0; v < VPL; ++v) acc[v] = fmaf(w[u], x[u][v], acc[v]);
+      for (int k = 0; k < IPL; ++k) jw[k] = jn[k];
+    }
+    // first trip indices of the next tile, then this tile's epilogue
+    load_idx(jw, nxt.b, nxt.e);
+    if (r >= 0) {
+      float sv[VPL];
+      RW::unpack(cur.self, sv);
+      const bool scaled = cur.di > 0.0f;
+      const float rdi = scaled ? __frcp_rn(cur.di) : 1.0f;
+      float o[VPL];
+#pragma unroll
+      for (int v = 0; v < VPL; ++v) {
+        const int cidx = lig * VPL + v;
+        const float mu = s_mu[cidx], is = s_is[cidx];
+        const float ti = scaled ? sv[v] * rdi : sv[v];
+        const float zi = (ti - mu) * is;
+        const float agg = is * fmaf(-mu, cur.wi, acc[v]);
+        const float y = fmaf(theta, zi, alpha * cur.di * agg);
+        const float t = tanhf(y);
+        qs[v] += __float2ll_rn(t * kQScale);
+        qq[v] += __float2ll_rn(t * t * kQScale);
+        o[v] = scaled ? cur.di * t : t;
       }
+      store_chunk_cs(Tout + (int64_t)r * D, o);
     }
-    // reduce-scatter over the slot bits (highest first), then all-reduce the rest
-#pragma unroll
-    for (int b = 0; b < RS; ++b) {
-      const int sb = ilog2(NS) - 1 - b;
-      constexpr int W0 = VPL;
-      const int half = W0 >> (b + 1);
-      const bool upper = (slot >> sb) & 1;
-#pragma unroll
-      for (int e = 0; e < (VPL >> (b + 1)); ++e) {
-        const float send = upper ? acc[e] : acc[half + e];
-        const float keep = upper ? acc[half + e] : acc[e];
-        const float recv = __shfl_xor_sync(0xffffffffu, send, G << sb);
-        acc[e] = keep + recv;
-      }
-    }
-#pragma unroll
-    for (int b = 0; b < AR; ++b) acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], G << b);
-#pragma unroll
-    for (int b = 0; b < ilog2(NS); ++b) wsum += __shfl_xor_sync(0xffffffffu, wsum, G << b);
-
-    // epilogue on this lane's EPL columns
-    const float di = __ldg(dinv + i);
-    float ti[EPL];
-    load_small<EPL>(Tin + i * D + cc, ti);
-    float t[EPL];
-#pragma unroll
-    for (int e = 0; e < EPL; ++e) {
-      const float zi = (ti[e] - mu_e[e]) * is_e[e];
-      const float agg = is_e[e] * fmaf(-mu_e[e], wsum, acc[e]);
-      const float y = fmaf(theta, zi, alpha * di * agg);
-      t[e] = tanhf(y);
-    }
-    if (owner) {
-      store_small<EPL>(Tout + i * D + cc, t);
-#pragma unroll
-      for (int e = 0; e < EPL; ++e) {
-        csum[e] += t[e];
-        csq[e] = fmaf(t[e], t[e], csq[e]);
-      }
-    }
+    r = r_n;
+    r_n = r_nn;
+    cur = nxt;
   }
 
-  // ---- column statistics: CTA partial, then the last CTA reduces all partials
-  if (owner) {
+  // ---- column statistics: exact integer sums over groups, warps, CTAs
 #pragma unroll
-    for (int e = 0; e < EPL; ++e) {
-      s_red[warp][cc + e] = csum[e];
-      s_red[warp][D + cc + e] = csq[e];
+  for (int m = G; m < 32; m <<= 1) {
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+      qs[v] += __shfl_xor_sync(0xffffffffu, qs[v], m);
+      qq[v] += __shfl_xor_sync(0xffffffffu, qq[v], m);
+    }
+  }
+  if (grp == 0) {
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+      s_red[warp][lig * VPL + v] = qs[v];
+      s_red[warp][D + lig * VPL + v] = qq[v];
     }
   }
   __syncthreads();
   for (int c = threadIdx.x; c < 2 * D; c += blockDim.x) {
-    float a = 0.0f;
+    long long a = 0;
 #pragma unroll
     for (int w = 0; w < kLayerWarps; ++w) a += s_red[w][c];
     partials[(int64_t)blockIdx.x * 2 * D + c] = a;
@@ -351,40 +555,40 @@ __global__ void __launch_bounds__(kLayerThreads) k_layer(
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // fixed-order reduction of gridDim.x partials: R threads per value, then R-way combine
   constexpr int R0 = kLayerThreads / (2 * D) > 0 ? kLayerThreads / (2 * D) : 1;
   constexpr int R = R0 < kLayerWarps ? R0 : kLayerWarps;
-  float* s_tot = &s_red[0][0];  // reuse: needs R * 2D <= kLayerWarps * 2D floats
-  static_assert(R <= kLayerWarps, "reduction scratch too small");
+  long long* s_tot = &s_red[0][0];  // reuse: R * 2D <= kLayerWarps * 2D
   for (int t = threadIdx.x; t < R * 2 * D; t += blockDim.x) {
-    const int c = t % (2 * D), r = t / (2 * D);
-    float a = 0.0f;
-    for (int b = r; b < (int)gridDim.x; b += R) a += __ldcg(partials + (int64_t)b * 2 * D + c);
-    s_tot[r * 2 * D + c] = a;
+    const int c = t % (2 * D), rr = t / (2 * D);
+    long long a = 0;
+    for (int b = rr; b < (int)gridDim.x; b += R) a += __ldcg(partials + (int64_t)b * 2 * D + c);
+    s_tot[rr * 2 * D + c] = a;
   }
   __syncthreads();
   for (int c = threadIdx.x; c < D; c += blockDim.x) {
-    float sa = 0.0f, qa = 0.0f;
-    for (int r = 0; r < R; ++r) {
-      sa += s_tot[r * 2 * D + c];
-      qa += s_tot[r * 2 * D + D + c];
+    long long sa = 0, qa = 0;
+    for (int rr = 0; rr < R; ++rr) {
+      sa += s_tot[rr * 2 * D + c];
+      qa += s_tot[rr * 2 * D + D + c];
     }
     const double n = (double)N;
-    const double mean = (double)sa / n;
+    const double st = (double)sa * (1.0 / (double)(1ll << kQBits));  // sum of t
+    const double sq = (double)qa * (1.0 / (double)(1ll << kQBits));  // sum of t^2
+    const double mean = st / n;
     const double denom = n - (double)ddof;
-    double var = denom > 0.0 ? ((double)qa - (double)sa * mean) / denom : 0.0;
+    double var = denom > 0.0 ? (sq - st * mean) / denom : 0.0;
     if (!(var > 0.0)) var = 0.0;
     const double sd = sqrt(var);
-    stats_out[c] = (float)mean;
-    stats_out[D + c] = sd > 0.0 ? (float)(1.0 / sd) : 0.0f;
+    stats_out[c0 + c] = (float)mean;
+    stats_out[d + c0 + c] = sd > 0.0 ? (float)(1.0 / sd) : 0.0f;
   }
   if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
 }
 
 // ------------------------------------------------------------------ output
 template <int D, typename S>
-__global__ void k_output(const S* __restrict__ T, const float* __restrict__ stats, int32_t N, int row_l2,
-                         float* __restrict__ out) {
+__global__ void k_output(const S* __restrict__ T, const float* __restrict__ dinv, const float* __restrict__ stats,
+                         int32_t N, int32_t dc, int row_l2, float* __restrict__ out) {
   constexpr int VPL = Store<S>::VPL;
   constexpr int G = D / VPL;  // lanes per row
   constexpr int RPW = 32 / G;  // rows per warp pass
@@ -396,18 +600,22 @@ __global__ void k_output(const S* __restrict__ T, const float* __restrict__ stat
     const int64_t i = base + sub;
     const bool ok = i < N;
     float v[VPL];
+    float di = 0.0f;
     if (ok) {
-      load_chunk(T + i * D + chunk * VPL, v);
+      load_chunk(T + blk_off(i, chunk * VPL, N, dc), v);
+      di = __ldg(dinv + i);
     } else {
 #pragma unroll
       for (int e = 0; e < VPL; ++e) v[e] = 0.0f;
     }
+    const float rdi = di > 0.0f ? __frcp_rn(di) : 1.0f;
     float o[VPL];
     float ss = 0.0f;
 #pragma unroll
     for (int e = 0; e < VPL; ++e) {
       const int c = chunk * VPL + e;
-      const float z = stats ? (v[e] - stats[c]) * stats[D + c] : v[e];
+      const float t = v[e] * rdi;
+      const float z = stats ? (t - stats[c]) * stats[D + c] : t;
       o[e] = 1.0f / (1.0f + expf(-z));  // sigmoid, Eq. 4
       ss = fmaf(o[e], o[e], ss);
     }
@@ -428,51 +636,80 @@ __global__ void k_output(const S* __restrict__ T, const float* __restrict__ stat
 }
 
 // ------------------------------------------------------------------ host dispatch
-constexpr int kUnroll = 4;
-
 template <int D, typename S>
 struct LayerCfg {
-  static int grid(int32_t N) {
-    static int per_sm = 0;
-    if (per_sm == 0) {
+  static int per_sm() {
+    static int v = 0;
+    if (v == 0) {
       int b = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_layer<D, S, kUnroll>, kLayerThreads, 0);
-      per_sm = b > 0 ? b : 1;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_layer<D, S>, kLayerThreads, 0);
+      v = b > 0 ? b : 1;
     }
-    int64_t want = ((int64_t)N + kLayerWarps - 1) / kLayerWarps;
-    int64_t cap = (int64_t)per_sm * num_sms();
+    return v;
+  }
+  static constexpr int GPW = 32 / (D / Store<S>::VPL);
+  // CTAs per chunk: one full wave, or fewer for small graphs
+  static int grid(int32_t N) {
+      const int64_t rows_per_cta = (int64_t)kLayerWarps * GPW;
+    const int64_t want = ((int64_t)N + rows_per_cta - 1) / rows_per_cta;
+    const int64_t cap = (int64_t)per_sm() * num_sms();
     return (int)std::max<int64_t>(1, std::min(want, cap));
   }
 };
 
 template <int D, typename S>
-igp_status layer_launch(const igp_graph* g, const void* Tin, void* Tout, const float* st_in, float* partials,
-                        float* st_out, unsigned* ticket, float alpha, float theta, int ddof, int grid,
+igp_status layer_launch(const igp_graph* g, const void* Tin, void* Tout, const float* st_in, long long* partials,
+                        float* st_out, unsigned* tickets, float alpha, float theta, int ddof, int grid, int d,
                         cudaStream_t s) {
-  k_layer<D, S, kUnroll><<<grid, kLayerThreads, 0, s>>>(g->row_ptr, g->col, g->dinv, (const S*)Tin, (S*)Tout, st_in,
-                                                        partials, st_out, ticket, g->N, alpha, theta, ddof);
+  dim3 gr(grid, d / D);
+  k_layer<D, S><<<gr, kLayerThreads, 0, s>>>(g->row_ptr, g->col, g->dinv, g->wsum, g->perm, (const S*)Tin, (S*)Tout,
+                                             st_in, partials, st_out, tickets, g->N, d, alpha, theta, ddof);
   return after_launch("k_layer");
 }
 
 template <int D, typename S>
-igp_status output_launch(const void* T, const float* st, int32_t N, int row_l2, float* out, cudaStream_t s) {
+igp_status output_launch(const void* T, const float* dinv, const float* st, int32_t N, int dc, int row_l2, float* out,
+                         cudaStream_t s) {
   constexpr int G = D / Store<S>::VPL;
   int64_t threads = (int64_t)N * G;
   int blocks = (int)std::min<int64_t>((threads + 255) / 256, (int64_t)num_sms() * 16);
-  k_output<D, S><<<std::max(blocks, 1), 256, 0, s>>>((const S*)T, st, N, row_l2, out);
+  k_output<D, S><<<std::max(blocks, 1), 256, 0, s>>>((const S*)T, dinv, st, N, dc, row_l2, out);
   return after_launch("k_output");
+}
+
+template <typename S>
+igp_status prescale_launch(const void* x, const float* dinv, int32_t N, int32_t d, int32_t dc, void* out,
+                           cudaStream_t s) {
+  int64_t total = (int64_t)N * d / Store<S>::VPL;
+  int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms() * 16);
+  k_prescale<S><<<std::max(blocks, 1), 256, 0, s>>>((const S*)x, dinv, N, d, dc, (S*)out);
+  return after_launch("k_prescale");
 }
 
 struct Ops {
   int (*grid)(int32_t);
-  igp_status (*layer)(const igp_graph*, const void*, void*, const float*, float*, float*, unsigned*, float, float,
-                      int, int, cudaStream_t);
-  igp_status (*output)(const void*, const float*, int32_t, int, float*, cudaStream_t);
+  igp_status (*layer)(const igp_graph*, const void*, void*, const float*, long long*, float*, unsigned*, float, float,
+                      int, int, int, cudaStream_t);
+  igp_status (*output)(const void*, const float*, const float*, int32_t, int, int, float*, cudaStream_t);
+  igp_status (*prescale)(const void*, const float*, int32_t, int32_t, int32_t, void*, cudaStream_t);
 };
 
 template <int D, typename S>
 Ops ops_for() {
-  return Ops{&LayerCfg<D, S>::grid, &layer_launch<D, S>, &output_launch<D, S>};
+  return Ops{&LayerCfg<D, S>::grid, &layer_launch<D, S>, &output_launch<D, S>, &prescale_launch<S>};
+}
+
+// L2 budget for the gathered chunk of T^(l-1): chunks of at most this many bytes.
+constexpr size_t kChunkBytes = 72ull << 20;
+
+// Column chunk width for a layer: the widest of d, d/2, d/4, .. whose N x width slice
+// fits the L2 budget, but never below 128 bytes per row: a gathered row segment is then
+// one full L2 line per request, and splitting it further multiplies the L1->L2 request
+// count (measured to cost more than the extra L2 hits gain).
+int chunk_width(int32_t N, int d, size_t sb) {
+  int w = d;
+  while ((size_t)N * w * sb > kChunkBytes && w * sb > 128) w >>= 1;
+  return w;
 }
 
 bool get_ops(int d, int storage, Ops* o) {
@@ -489,52 +726,98 @@ bool get_ops(int d, int storage, Ops* o) {
 
 }  // namespace
 
+igp_status ensure_perm(igp_graph* g, cudaStream_t s) {
+  if (g->perm) return IGP_OK;
+  const int32_t N = g->N;
+  const int64_t nb = (int64_t)g->max_deg + 1;
+  void* p = nullptr;
+  IGP_TRY(dev_alloc(&p, (size_t)N * sizeof(int32_t), s));
+  g->perm = (int32_t*)p;
+  void* t = nullptr;
+  const int64_t ntiles = (nb + 1 + 8191) / 8192;
+  IGP_TRY(dev_alloc(&t, (size_t)(3 * (nb + 1) + ntiles) * sizeof(int), s));
+  int* hist = (int*)t;
+  int* off = hist + (nb + 1);
+  int* cur = off + (nb + 1);
+  int* tmp = cur + (nb + 1);
+  igp_status st = IGP_OK;
+  if (cudaMemsetAsync(hist, 0, (nb + 1) * sizeof(int), s) != cudaSuccess ||
+      cudaMemsetAsync(cur, 0, (nb + 1) * sizeof(int), s) != cudaSuccess)
+    st = cuda_status(cudaGetLastError(), "memset", __FILE__, __LINE__);
+  const int blocks = (int)(((int64_t)N + kPermRowsPerBlock - 1) / kPermRowsPerBlock);
+  const size_t smem = nb <= kPermSmemBins ? (size_t)nb * sizeof(int) : 0;
+  if (st == IGP_OK) {
+    k_deg_hist<<<blocks, 512, smem, s>>>(g->row_ptr, N, g->max_deg, hist);
+    st = after_launch("k_deg_hist");
+  }
+  if (st == IGP_OK) st = exclusive_scan(hist, off, nb + 1, tmp, s);
+  if (st == IGP_OK) {
+    k_deg_scatter<<<blocks, 512, smem, s>>>(g->row_ptr, N, g->max_deg, off, cur, g->perm);
+    st = after_launch("k_deg_scatter");
+  }
+  dev_free(t, s);
+  if (st != IGP_OK) {
+    dev_free(g->perm, s);
+    g->perm = nullptr;
+  }
+  return st;
+}
+
 igp_status compute_dinv(igp_graph* g, double tau, double eps, cudaStream_t s, Profile* prof) {
   if (g->dinv_valid && g->dinv_tau == tau && g->dinv_eps == eps) return IGP_OK;
   if (!g->dinv) {
     void* p = nullptr;
-    IGP_TRY(dev_alloc(&p, (size_t)g->N * sizeof(float), s));
+    IGP_TRY(dev_alloc(&p, (size_t)g->N * 2 * sizeof(float), s));
     g->dinv = (float*)p;
+    g->wsum = g->dinv + g->N;
   }
   PhaseTimer pt(prof, IGP_PHASE_DINV, s);
   int blocks = (int)std::min<int64_t>(((int64_t)g->N + 255) / 256, (int64_t)num_sms() * 8);
   k_dinv<<<std::max(blocks, 1), 256, 0, s>>>(g->row_ptr, g->N, tau, eps, g->dinv);
   IGP_TRY(after_launch("k_dinv"));
+  int wblocks = (int)std::min<int64_t>(((int64_t)g->N * 32 + 255) / 256, (int64_t)num_sms() * 16);
+  k_wsum<<<std::max(wblocks, 1), 256, 0, s>>>(g->row_ptr, g->col, g->dinv, g->N, g->wsum);
+  IGP_TRY(after_launch("k_wsum"));
   g->dinv_valid = true;
   g->dinv_tau = tau;
   g->dinv_eps = eps;
   return IGP_OK;
 }
 
-igp_status launch_theta(uint64_t seed, int32_t N, int32_t d, float xs, int storage, void* out, cudaStream_t s) {
+igp_status launch_theta(uint64_t seed, int32_t N, int32_t d, int32_t dc, float xs, int storage, const float* dinv,
+                        void* out, cudaStream_t s) {
   int64_t total = (int64_t)N * (d / 8);
   int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms() * 16);
   blocks = std::max(blocks, 1);
   if (storage == IGP_STORE_BF16)
-    k_theta<__nv_bfloat16><<<blocks, 256, 0, s>>>(seed, N, d, xs, (__nv_bfloat16*)out);
+    k_theta<__nv_bfloat16><<<blocks, 256, 0, s>>>(seed, N, d, dc, xs, dinv, (__nv_bfloat16*)out);
   else
-    k_theta<float><<<blocks, 256, 0, s>>>(seed, N, d, xs, (float*)out);
+    k_theta<float><<<blocks, 256, 0, s>>>(seed, N, d, dc, xs, dinv, (float*)out);
   return after_launch("k_theta");
 }
 
 igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed, float* out_dev,
                    const igp_embed_opts& o, cudaStream_t s) {
   Profile* prof = o.profile ? &o.profile->prof : nullptr;
-  Ops ops;
-  if (!get_ops(d, o.storage, &ops)) {
+  Ops ops, lops;
+  const int32_t N = g->N;
+  const size_t sb = o.storage == IGP_STORE_BF16 ? 2 : 4;
+  const int dc = o.chunk_cols > 0 ? o.chunk_cols : chunk_width(N, d, sb);  // columns per layer chunk
+  if (!get_ops(d, o.storage, &ops) || !get_ops(dc, o.storage, &lops)) {
     set_error("igp_embed: d=%d unsupported (8, 16, 32, 64, 128)", d);
     return IGP_E_INVAL;
   }
+  const int nchunks = d / dc;
   IGP_TRY(compute_dinv(g, tau, o.eps, s, prof));
-  const int32_t N = g->N;
-  const size_t sb = o.storage == IGP_STORE_BF16 ? 2 : 4;
-  const int grid = ops.grid(N);
-  // workspace: T0 | T1 | stats[2][2d] | partials[grid][2d] | ticket
+  const int grid = lops.grid(N);
+  IGP_TRY(ensure_perm(g, s));
+  // workspace: T0 | T1 | stats[2][2d] | partials[nchunks][grid][2dc] | tickets[nchunks]
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t bT = al((size_t)N * d * sb);
   const size_t bS = al(2 * 2 * (size_t)d * sizeof(float));
-  const size_t bP = al((size_t)grid * 2 * d * sizeof(float));
-  const size_t need = 2 * bT + bS + bP + 256;
+  const size_t bP = al((size_t)nchunks * grid * 2 * dc * sizeof(long long));
+  const size_t bK = al((size_t)nchunks * sizeof(unsigned));
+  const size_t need = 2 * bT + bS + bP + bK;
   if (g->ws_bytes < need) {
     if (g->ws) dev_free(g->ws, s);
     g->ws = nullptr;
@@ -548,29 +831,32 @@ igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed
   void* T0 = base;
   void* T1 = base + bT;
   float* stats = (float*)(base + 2 * bT);
-  float* partials = (float*)(base + 2 * bT + bS);
-  unsigned* ticket = (unsigned*)(base + 2 * bT + bS + bP);
-  IGP_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s) == cudaSuccess ? IGP_OK : IGP_E_CUDA);
+  long long* partials = (long long*)(base + 2 * bT + bS);
+  unsigned* tickets = (unsigned*)(base + 2 * bT + bS + bP);
+  IGP_TRY_CUDA(cudaMemsetAsync(tickets, 0, nchunks * sizeof(unsigned), s));
 
-  const double xs = o.x_scale > 0 ? o.x_scale : 1.0 / std::sqrt((double)d);
-  const void* cur = o.x_in;
-  if (!cur) {
+  {
     PhaseTimer pt(prof, IGP_PHASE_THETA, s);
-    IGP_TRY(launch_theta(seed, N, d, (float)xs, o.storage, T0, s));
-    cur = T0;
+    if (o.x_in) {
+      IGP_TRY(ops.prescale(o.x_in, g->dinv, N, d, dc, T0, s));
+    } else {
+      const double xs = o.x_scale > 0 ? o.x_scale : 1.0 / std::sqrt((double)d);
+      IGP_TRY(launch_theta(seed, N, d, dc, (float)xs, o.storage, g->dinv, T0, s));
+    }
   }
+  const void* cur = T0;
   const float* st_prev = nullptr;
   for (int32_t l = 1; l <= L; ++l) {
     void* dst = (cur == T0) ? T1 : T0;
     float* st = stats + (size_t)(l & 1) * 2 * d;
     PhaseTimer pt(prof, IGP_PHASE_LAYER, s);
-    IGP_TRY(ops.layer(g, cur, dst, st_prev, partials, st, ticket, (float)o.alpha, (float)o.theta, o.znorm_ddof,
-                      grid, s));
+    IGP_TRY(lops.layer(g, cur, dst, st_prev, partials, st, tickets, (float)o.alpha, (float)o.theta, o.znorm_ddof,
+                       grid, d, s));
     cur = dst;
     st_prev = st;
   }
   PhaseTimer pt(prof, IGP_PHASE_OUTPUT, s);
-  return ops.output(cur, st_prev, N, o.out_row_l2, out_dev, s);
+  return ops.output(cur, g->dinv, st_prev, N, dc, o.out_row_l2, out_dev, s);
 }
 
 }  // namespace igp

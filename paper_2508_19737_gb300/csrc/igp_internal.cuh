@@ -74,8 +74,11 @@ struct igp_graph {
   int device = 0;
   int32_t* row_ptr = nullptr;  // device [N+1]
   int32_t* col = nullptr;      // device [nnz]
-  // Eq. 1 factors for the last (tau, eps) asked for
+  // Eq. 1 factors for the last (tau, eps) asked for, and w_i = sum_{j in N(i)} dinv_j
   float* dinv = nullptr;       // device [N]
+  float* wsum = nullptr;       // device [N], same allocation as dinv
+  // rows in order of decreasing degree (the layer kernel's processing order)
+  int32_t* perm = nullptr;
   double dinv_tau = 0, dinv_eps = 0;
   bool dinv_valid = false;
   // FFP workspace (grown on demand, kept until free)
@@ -87,13 +90,17 @@ struct igp_graph {
 };
 
 namespace igp {
+// csr_build.cu: exclusive prefix sum of n >= 1 ints; tmp holds ceil(n / 8192) ints.
+igp_status exclusive_scan(const int* in, int* out, int64_t n, int* tmp, cudaStream_t s);
 // csr_build.cu: CSR of the undirected edge list (device inputs), into g (empty).
 igp_status build_csr(const int32_t* src, const int32_t* dst, int64_t M, int32_t N, cudaStream_t s,
                      igp_graph* g);
 // ffp.cu
 igp_status compute_dinv(igp_graph* g, double tau, double eps, cudaStream_t s, Profile* prof);
-igp_status launch_theta(uint64_t seed, int32_t N, int32_t d, float x_scale, int storage, void* out,
-                        cudaStream_t s);
+// Theta (Alg. 1, line 2) into `out` in the storage type, in column blocks of dc columns
+// (dc = d: row-major), multiplied row-wise by dinv if non-NULL.
+igp_status launch_theta(uint64_t seed, int32_t N, int32_t d, int32_t dc, float x_scale, int storage,
+                        const float* dinv, void* out, cudaStream_t s);
 igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed, float* out_dev,
                    const igp_embed_opts& o, cudaStream_t s);
 }  // namespace igp

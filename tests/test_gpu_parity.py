@@ -149,7 +149,26 @@ def test_every_width_parity(api, d, storage):
     assert row_rel_err(got, ref) <= TOL[storage]
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_chunked_layers_equal_unchunked(api, storage):
+    import torch
+    g = synth.dcsbm(20000, 16, 20, 2.5, 5, seed=11)
+    gr = api.graph_build(g.src, g.dst, g.N)
+    outs = []
+    for cc in (0, 32, 16, 8):
+        o = torch.empty((g.N, 64), dtype=torch.float32, device="cuda")
+        api.embed(gr, -0.5, 8, 64, 5, out=o, storage=storage, chunk_cols=cc)
+        outs.append(o.cpu().numpy())
+    gr.free()
+    for o in outs[1:]:  # column passes change nothing: the statistics are exact integer sums
+        assert np.array_equal(o, outs[0])
+    with pytest.raises(api.IgpError):
+        api.embed(api.graph_build(g.src, g.dst, g.N), -0.5, 2, 64, 0, chunk_cols=24)
+
+
 @pytest.mark.parametrize("opts", [
+    dict(chunk_cols=16),                  # four column passes per layer
+    dict(chunk_cols=8),                   # one 32-byte slice per row, four passes
     dict(znorm_ddof=0),
     dict(out_row_l2=True),
     dict(alpha=-0.5, theta=0.7),          # high-pass filter (Eq. 2, alpha < 0)
