@@ -151,6 +151,27 @@ igp_status igp_generate_x(uint64_t seed, int32_t N, int32_t d, double x_scale, f
 igp_status igp_embed(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed, float* out,
                      const igp_embed_opts* opts, void* stream);
 
+/*
+ * igp_embed without any memory allocation. (The paper has no counterpart: this serves callers that
+ * may not allocate device memory at the moment they call, e.g. code recording a CUDA stream capture,
+ * where cudaMalloc is not allowed, an allocator or memory-manager hook that must not re-enter the
+ * CUDA allocator, or a loop that must keep a fixed memory footprint.)
+ *   row_ptr, col : DEVICE CSR of the graph, [N+1] and [row_ptr[N]] int32, in the form igp_graph_export
+ *                  writes (symmetric, no self-loops, ids in [0, N)); it is trusted, not checked
+ *   out          : DEVICE N x d fp32 output
+ *   tau, L, d, seed, opts : as for igp_embed; opts->profile and opts->chunk_cols must be 0
+ * Same result as igp_embed on the graph built from that CSR. All temporaries live in a fixed
+ * 16 MiB device array inside the library, reserved on every GPU that loads the library until the
+ * process exits; sizes whose temporaries do not fit (about 2 N d storage-size bytes plus 12 N bytes
+ * and the column-statistics partials) are rejected with IGP_E_INVAL before any GPU work. The call
+ * issues no cudaMalloc, cudaFree or other allocating routine. The first call on each device looks
+ * up that device's address of the array (cudaGetSymbolAddress); make it before any stream capture.
+ * All calls share the array: calls whose GPU work overlaps (other streams, other threads) race, so
+ * serialise them. Asynchronous on `stream`.
+ */
+igp_status igp_embed_noalloc(const int32_t* row_ptr, const int32_t* col, int32_t N, double tau, int32_t L, int32_t d,
+                             uint64_t seed, float* out, const igp_embed_opts* opts, void* stream);
+
 /* Per-phase device timing. Events are recorded on the call's stream around each phase. */
 igp_status igp_profile_create(igp_profile** p);
 void igp_profile_free(igp_profile* p);

@@ -80,6 +80,9 @@ _SIGS = {
                                         ctypes.c_void_p, ctypes.c_void_p]),
     "igp_embed": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(EmbedOpts), ctypes.c_void_p]),
+    "igp_embed_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
+                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p,
+                                           ctypes.POINTER(EmbedOpts), ctypes.c_void_p]),
     "igp_profile_create": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_void_p)]),
     "igp_profile_free": (None, [ctypes.c_void_p]),
     "igp_profile_read": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
@@ -271,4 +274,16 @@ def embed(g, tau, L, d, seed, out=None, opts=None, stream=None, **kw):
         out = np.empty((g.N, d), dtype=np.float32)
     _check(lib().igp_embed(g.handle, float(tau), int(L), int(d), int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out),
                            ctypes.byref(opts), _stream(stream)))
+    return out
+
+
+def embed_noalloc(row_ptr, col, N, tau, L, d, seed, out, opts=None, stream=None, **kw):
+    """igp_embed_noalloc: one FFP on a caller-held device CSR into a device `out`, using only the
+    library's fixed scratch array (for callers that must not allocate during the call)."""
+    if opts is None:
+        opts = embed_opts(**kw)
+    elif kw:
+        raise ValueError("give either opts or keyword options")
+    _check(lib().igp_embed_noalloc(_ptr(row_ptr), _ptr(col), int(N), float(tau), int(L), int(d),
+                                   int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out), ctypes.byref(opts), _stream(stream)))
     return out

@@ -30,6 +30,7 @@
 //     in fp64. Integer sums make the result independent of the row order.
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 
 #include "igp_internal.cuh"
 
@@ -860,3 +861,146 @@ igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed
 }
 
 }  // namespace igp
+
+// ============================================================================
+// igp_embed_noalloc: one FFP that allocates nothing.
+//
+// Some callers cannot allocate device memory while they call into this library:
+// code running inside a CUDA stream capture (cudaMalloc is not capturable), an
+// allocator hook or custom memory manager that must not re-enter the CUDA
+// allocator, or a real-time loop that has to keep a fixed memory footprint. This
+// entry point serves them: the caller passes the CSR, the output and a stream; all
+// temporaries live in one fixed device array that is part of the library image.
+//
+// The array below is reserved on every GPU that loads the library and stays
+// reserved until the process exits. Every call shares it, so calls whose GPU work
+// overlaps (on different streams, or from different host threads) race with each
+// other; serialise them. It keeps the last call's contents; what a call needs zeroed
+// (the completion tickets of the column statistics) it clears itself.
+// ============================================================================
+namespace igp {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 16ull << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+__global__ void k_iota(int32_t N, int32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int32_t)i;
+}
+
+// Device address of g_noalloc_scratch on the current device (host code may not use the
+// symbol itself: on the host it names a stand-in, not device memory).
+igp_status noalloc_scratch(void** ptr) {
+  static std::mutex mu;
+  static void* addr[64] = {};
+  int dev = 0;
+  IGP_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("igp_embed_noalloc: device ordinal %d out of range", dev);
+    return IGP_E_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+    addr[dev] = p;
+  }
+  *ptr = addr[dev];
+  return IGP_OK;
+}
+
+}  // namespace
+}  // namespace igp
+
+extern "C" igp_status igp_embed_noalloc(const int32_t* row_ptr, const int32_t* col, int32_t N, double tau,
+                                        int32_t L, int32_t d, uint64_t seed, float* out,
+                                        const igp_embed_opts* opts, void* stream) {
+  using namespace igp;
+  clear_error();
+  igp_embed_opts o;
+  if (opts)
+    o = *opts;
+  else
+    igp_embed_opts_init(&o);
+  if (!row_ptr || !col || !out || N < 1) {
+    set_error("igp_embed_noalloc: need device row_ptr, col and out, and N >= 1");
+    return IGP_E_INVAL;
+  }
+  if (!std::isfinite(tau) || L < 0 || L > 10000 || !std::isfinite(o.alpha) || !std::isfinite(o.theta) ||
+      !(o.eps > 0) || !std::isfinite(o.eps) || (o.znorm_ddof != 0 && o.znorm_ddof != 1) ||
+      (o.storage != IGP_STORE_F32 && o.storage != IGP_STORE_BF16) || !std::isfinite(o.x_scale)) {
+    set_error("igp_embed_noalloc: invalid tau, L or options");
+    return IGP_E_INVAL;
+  }
+  if (o.profile || o.chunk_cols != 0) {
+    set_error("igp_embed_noalloc: opts->profile and opts->chunk_cols are not supported here (leave them 0)");
+    return IGP_E_INVAL;
+  }
+  Ops ops;
+  if (!get_ops(d, o.storage, &ops)) {
+    set_error("igp_embed_noalloc: d=%d unsupported (8, 16, 32, 64, 128)", d);
+    return IGP_E_INVAL;
+  }
+  if (!is_device_ptr(row_ptr) || !is_device_ptr(col) || !is_device_ptr(out) ||
+      (o.x_in && !is_device_ptr(o.x_in))) {
+    set_error("igp_embed_noalloc: row_ptr, col, out (and opts->x_in) must be device memory");
+    return IGP_E_INVAL;
+  }
+  // scratch layout: dinv | w | perm | T0 | T1 | stats[2][2d] | partials[grid][2d] | ticket
+  const size_t sb = o.storage == IGP_STORE_BF16 ? 2 : 4;
+  const int grid = ops.grid(N);
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t bN = al((size_t)N * 4);
+  const size_t bT = al((size_t)N * d * sb);
+  const size_t bS = al(2 * 2 * (size_t)d * sizeof(float));
+  const size_t bP = al((size_t)grid * 2 * d * sizeof(long long));
+  const size_t need = 3 * bN + 2 * bT + bS + bP + 256;
+  if (need > kNoAllocScratchBytes) {
+    set_error("igp_embed_noalloc: N=%d, d=%d needs %zu bytes of scratch, more than the fixed %zu (16 MiB); "
+              "use igp_embed for this size",
+              N, d, need, kNoAllocScratchBytes);
+    return IGP_E_INVAL;
+  }
+  void* scratch = nullptr;
+  IGP_TRY(noalloc_scratch(&scratch));
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)scratch;
+  // a non-owning view of the caller's CSR with the scratch-resident per-graph arrays
+  igp_graph gv;
+  gv.N = N;
+  gv.row_ptr = const_cast<int32_t*>(row_ptr);
+  gv.col = const_cast<int32_t*>(col);
+  gv.dinv = (float*)base;
+  gv.wsum = (float*)(base + bN);
+  gv.perm = (int32_t*)(base + 2 * bN);
+  void* T0 = base + 3 * bN;
+  void* T1 = base + 3 * bN + bT;
+  float* stats = (float*)(base + 3 * bN + 2 * bT);
+  long long* partials = (long long*)(base + 3 * bN + 2 * bT + bS);
+  unsigned* ticket = (unsigned*)(base + 3 * bN + 2 * bT + bS + bP);
+  IGP_TRY_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s));
+
+  IGP_TRY(compute_dinv(&gv, tau, o.eps, s, nullptr));  // writes dinv and w in place
+  const int blocks = (int)std::min<int64_t>(((int64_t)N + 255) / 256, (int64_t)num_sms() * 8);
+  k_iota<<<std::max(blocks, 1), 256, 0, s>>>(N, gv.perm);  // rows in their own order
+  IGP_TRY(after_launch("k_iota"));
+  if (o.x_in) {
+    IGP_TRY(ops.prescale(o.x_in, gv.dinv, N, d, d, T0, s));
+  } else {
+    const double xs = o.x_scale > 0 ? o.x_scale : 1.0 / std::sqrt((double)d);
+    IGP_TRY(launch_theta(seed, N, d, d, (float)xs, o.storage, gv.dinv, T0, s));
+  }
+  const void* cur = T0;
+  const float* st_prev = nullptr;
+  for (int32_t l = 1; l <= L; ++l) {
+    void* dst = (cur == T0) ? T1 : T0;
+    float* st = stats + (size_t)(l & 1) * 2 * d;
+    IGP_TRY(ops.layer(&gv, cur, dst, st_prev, partials, st, ticket, (float)o.alpha, (float)o.theta, o.znorm_ddof,
+                      grid, d, s));
+    cur = dst;
+    st_prev = st;
+  }
+  return ops.output(cur, gv.dinv, st_prev, N, d, o.out_row_l2, out, s);
+}
