@@ -78,6 +78,9 @@ typedef struct igp_embed_opts {
                           whose N x width slice of the activations fits ~72 MB of L2, keeping at
                           least 128 bytes per row. Otherwise a power of two dividing d, >= 8, with
                           at least 16 bytes per row. Result-neutral (exact integer statistics). */
+  int64_t l2_hot_bytes;/* L2 share for the most-gathered (highest-degree) activation rows, which a
+                          layer loads with an evict-last policy and the rest evict-first; 0 (default)
+                          = 48 MiB, < 0 = no L2 priority hints. Result-neutral. */
   const void* x_in;    /* NULL: Theta from `seed`. Else a DEVICE pointer to N x d row-major values in
                           the storage type, used as Z^(0) instead (not modified). */
   igp_profile* profile;/* NULL, or a profile that records per-phase device times of this call */

@@ -53,6 +53,7 @@ class EmbedOpts(ctypes.Structure):
         ("storage", ctypes.c_int32),
         ("out_row_l2", ctypes.c_int32),
         ("chunk_cols", ctypes.c_int32),
+        ("l2_hot_bytes", ctypes.c_int64),
         ("x_in", ctypes.c_void_p),
         ("profile", ctypes.c_void_p),
     ]
@@ -148,7 +149,7 @@ def launch_count():
 
 
 def embed_opts(alpha=1.0, theta=0.1, eps=1e-3, x_scale=0.0, znorm_ddof=1, storage="f32", out_row_l2=False,
-               x_in=None, profile=None, chunk_cols=0):
+               x_in=None, profile=None, chunk_cols=0, l2_hot_bytes=0):
     o = EmbedOpts()
     lib().igp_embed_opts_init(ctypes.byref(o))
     o.alpha, o.theta, o.eps, o.x_scale = alpha, theta, eps, x_scale
@@ -156,6 +157,7 @@ def embed_opts(alpha=1.0, theta=0.1, eps=1e-3, x_scale=0.0, znorm_ddof=1, storag
     o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     o.out_row_l2 = 1 if out_row_l2 else 0
     o.chunk_cols = int(chunk_cols)
+    o.l2_hot_bytes = int(l2_hot_bytes)
     o.x_in = _ptr(x_in)
     o.profile = profile.handle if profile is not None else None
     return o

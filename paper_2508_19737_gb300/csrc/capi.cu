@@ -281,7 +281,18 @@ igp_status igp_degree_factors(igp_graph* g, double tau, double eps, float* dinv,
   cudaStream_t s = (cudaStream_t)stream;
   IGP_TRY(graph_wait(g, s));
   IGP_TRY(compute_dinv(g, tau, eps, s, nullptr));
-  IGP_TRY(copy_out(dinv, g->dinv, (size_t)g->N * sizeof(float), s));
+  const size_t bytes = (size_t)g->N * sizeof(float);
+  igp_status st;
+  if (is_device_ptr(dinv)) {
+    st = dinv_original_order(g, dinv, s);
+  } else {
+    void* tmp = nullptr;
+    IGP_TRY(dev_alloc(&tmp, bytes, s));
+    st = dinv_original_order(g, (float*)tmp, s);
+    if (st == IGP_OK) st = copy_out(dinv, tmp, bytes, s);
+    dev_free(tmp, s);
+  }
+  if (st != IGP_OK) return st;
   return graph_mark(g, s);
 }
 
@@ -296,7 +307,8 @@ void igp_graph_free(igp_graph* g) {
   if (g->row_ptr) cudaFreeAsync(g->row_ptr, s);
   if (g->col) cudaFreeAsync(g->col, s);
   if (g->dinv) cudaFreeAsync(g->dinv, s);
-  if (g->perm) cudaFreeAsync(g->perm, s);
+  if (g->perm) cudaFreeAsync(g->perm, s);  // also holds inv and lrow_ptr
+  if (g->lcol) cudaFreeAsync(g->lcol, s);
   if (g->ws) cudaFreeAsync(g->ws, s);
   if (g->done) cudaEventDestroy(g->done);
   cudaGetLastError();
@@ -313,10 +325,10 @@ igp_status igp_generate_x(uint64_t seed, int32_t N, int32_t d, double x_scale, f
   cudaStream_t s = (cudaStream_t)stream;
   const double xs = x_scale > 0 ? x_scale : 1.0 / std::sqrt((double)d);
   const size_t bytes = (size_t)N * d * sizeof(float);
-  if (is_device_ptr(out)) return launch_theta(seed, N, d, d, (float)xs, IGP_STORE_F32, nullptr, out, s);
+  if (is_device_ptr(out)) return launch_theta(seed, N, d, d, (float)xs, IGP_STORE_F32, nullptr, nullptr, out, s);
   void* tmp = nullptr;
   IGP_TRY(dev_alloc(&tmp, bytes, s));
-  igp_status st = launch_theta(seed, N, d, d, (float)xs, IGP_STORE_F32, nullptr, tmp, s);
+  igp_status st = launch_theta(seed, N, d, d, (float)xs, IGP_STORE_F32, nullptr, nullptr, tmp, s);
   if (st == IGP_OK) st = copy_out(out, tmp, bytes, s);
   dev_free(tmp, s);
   return st;

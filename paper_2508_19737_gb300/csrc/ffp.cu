@@ -1,30 +1,37 @@
 // The feed-forward propagation (FFP) of InfraredGP, Alg. 1 lines 1-6:
 //   k_dinv        Eq. 1 degree correction D_tau and D_tau^{-1/2} (fp64, rounded to fp32)
 //   k_wsum        w_i = sum_{j in N(i)} dinv_j (fp32), once per graph and tau
-//   k_deg_*       rows in order of decreasing degree, once per graph
+//   k_deg_*, k_invert, k_lrow_count, k_relabel
+//                 the "layer CSR": the graph relabelled by decreasing degree, once per graph
 //   k_theta       Z^(0) = Theta ~ N(0, 1/d): Philox4x64-10 + Box-Muller (Alg. 1, line 2)
 //   k_layer       one Eq. 4 layer: T^(l) = tanh(theta Z + alpha Ahat Z), Z = ZNorm(T^(l-1)),
 //                 fused with the column statistics of T^(l) that the next ZNorm needs
 //   k_output      Z~ = sigmoid(ZNorm(T^(L))) (Eq. 4), optional row L2 normalisation
 //
-// Storage: row i of every N x d activation buffer holds s_i = dinv_i * t_i (t_i itself
-// when dinv_i = 0, an isolated node at tau = 0). With Z = ZNorm(T) = (T - mu) inv_s,
-//     sum_j dinv_j z_j = inv_s (sum_j s_j - mu w_i),
+// Storage: row k of every N x d activation buffer holds s_k = dinv_k * t_k (t_k itself
+// when dinv_k = 0, an isolated node at tau = 0). With Z = ZNorm(T) = (T - mu) inv_s,
+//     sum_j dinv_j z_j = inv_s (sum_j s_j - mu w_k),
 // so a layer gathers neighbour rows and only adds them: no per-neighbour degree
-// factor, no per-neighbour normalisation; the self term uses t_i = s_i / dinv_i.
+// factor, no per-neighbour normalisation; the self term uses t_k = s_k / dinv_k.
+//
+// Relabelling: the layers run on the graph with its nodes renumbered by decreasing
+// degree (the FFP commutes with a relabelling; Theta is still drawn for the original
+// ids and the output is written back to the original rows). Then a warp's consecutive
+// rows have (nearly) equal degree, all per-row data is read and written sequentially,
+// and the most-gathered rows are the lowest ids.
 //
 // Layer kernel (bandwidth-bound sparse gather, no tensor cores):
 //   * a group of G lanes owns one row; each lane owns 16 bytes of it (8 bf16 or 4 fp32
-//     values), so a neighbour row is G coalesced 16-byte loads;
-//   * rows are visited in decreasing-degree order in warp tiles of 32/G rows, so the
-//     groups of a warp have (nearly) the same trip count and stay converged;
+//     values), so a neighbour row is G coalesced 16-byte loads; a warp takes tiles of
+//     32/G consecutive rows, so its groups have equal trip counts and stay converged;
 //   * kChunk neighbour rows per group are in flight per trip; the next trip's column
-//     indices and the next tile's rows (perm entry, row bounds, self row, dinv, w) are
-//     prefetched while the current trip is gathered;
-//   * wide rows are split into column chunks (blockIdx.y) so that the gathered slice of
-//     T^(l-1) stays L2-resident; column indices are loaded with an evict-first policy
-//     and outputs are stored streaming;
-//   * epilogue per row: self term, tanh, store s_i, and exact integer column sums of t
+//     indices and the next tile's row data are prefetched during the current trip;
+//   * L2 policy: rows below the hot bound (the highest-degree rows, sized to a share of
+//     L2) are gathered evict-last, the others evict-first; column indices are loaded
+//     evict-first; outputs of cold rows are stored streaming;
+//   * wide rows can be split into column chunks (blockIdx.y) over a column-blocked
+//     activation layout so that the gathered slice of T^(l-1) fits L2;
+//   * epilogue per row: self term, tanh, store s_k, and exact integer column sums of t
 //     and t^2 (fixed point 2^-30); a warp/CTA reduction gives one partial per CTA and
 //     the last CTA to finish (ticket counter) adds them up and forms mean and 1/std
 //     in fp64. Integer sums make the result independent of the row order.
@@ -152,6 +159,16 @@ __device__ __forceinline__ int ld_stream(const int* p, uint64_t pol) {
   asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
   return v;
 }
+__device__ __forceinline__ uint64_t evict_normal_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t evict_last_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
 // Rows written by a layer are read again only by the next layer: streaming stores.
 __device__ __forceinline__ void store_chunk_cs(float* p, const float (&v)[4]) {
   __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
@@ -220,16 +237,17 @@ __device__ __forceinline__ void theta8(uint64_t seed, uint64_t i, uint64_t q, fl
 }
 
 // Theta, stored as dinv_i * Theta_i when dinv is given (the layer storage convention).
+// Row i of `out` holds the draw of original node rowid[i] (rowid NULL: node i).
 template <typename S>
 __global__ void k_theta(uint64_t seed, int32_t N, int32_t d, int32_t dc, float xs, const float* __restrict__ dinv,
-                        S* __restrict__ out) {
+                        const int32_t* __restrict__ rowid, S* __restrict__ out) {
   const int nq = d >> 3;
   const int64_t total = (int64_t)N * nq;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t / nq;
     const int q = (int)(t - i * nq);
     float z[8];
-    theta8(seed, (uint64_t)i, (uint64_t)q, xs, z);
+    theta8(seed, (uint64_t)(rowid ? __ldg(rowid + i) : i), (uint64_t)q, xs, z);
     if (dinv) {
       const float di = __ldg(dinv + i);
       if (di > 0.0f) {
@@ -326,18 +344,58 @@ __global__ void k_deg_scatter(const int32_t* __restrict__ row_ptr, int32_t N, in
   }
 }
 
+// inv[perm[k]] = k
+__global__ void k_invert(const int32_t* __restrict__ perm, int32_t N, int32_t* __restrict__ inv) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+    inv[perm[k]] = (int32_t)k;
+}
+// cnt[k] = degree of original row perm[k]; cnt[N] = 0
+__global__ void k_lrow_count(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ perm, int32_t N,
+                             int* __restrict__ cnt) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= N; k += (int64_t)gridDim.x * blockDim.x) {
+    if (k == N) {
+      cnt[k] = 0;
+    } else {
+      const int r = perm[k];
+      cnt[k] = row_ptr[r + 1] - row_ptr[r];
+    }
+  }
+}
+// Row k of the relabelled graph: the neighbours of original row perm[k], renamed by inv,
+// in the original (increasing original id) order. One warp per row.
+__global__ void k_relabel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                          const int32_t* __restrict__ perm, const int32_t* __restrict__ inv,
+                          const int32_t* __restrict__ lrow_ptr, int32_t N, int32_t* __restrict__ lcol) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < N;
+       k += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int r = perm[k];
+    const int b = row_ptr[r], n = row_ptr[r + 1] - b;
+    const int o = lrow_ptr[k];
+    for (int t = lane; t < n; t += 32) lcol[o + t] = inv[col[b + t]];
+  }
+}
+// dst[i] = src[idx[i]]
+__global__ void k_gather_f32(const float* __restrict__ src, const int32_t* __restrict__ idx, int32_t N,
+                             float* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[idx[i]];
+}
+
 // A caller-supplied Z^(0) in the storage type, copied into the row-scaled storage.
+// Row i of `out` takes row rowid[i] of x (rowid NULL: row i).
 template <typename S>
-__global__ void k_prescale(const S* __restrict__ x, const float* __restrict__ dinv, int32_t N, int32_t d,
-                           int32_t dc, S* __restrict__ out) {
+__global__ void k_prescale(const S* __restrict__ x, const float* __restrict__ dinv,
+                           const int32_t* __restrict__ rowid, int32_t N, int32_t d, int32_t dc, S* __restrict__ out) {
   constexpr int VPL = Store<S>::VPL;
   const int nc = d / VPL;
   const int64_t total = (int64_t)N * nc;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t / nc;
     const int c = (int)(t - i * nc) * VPL;
+    const int64_t src = rowid ? (int64_t)__ldg(rowid + i) : i;
     float v[VPL];
-    load_chunk(x + t * VPL, v);
+    load_chunk(x + src * d + c, v);
     const float di = __ldg(dinv + i);
     if (di > 0.0f) {
 #pragma unroll
@@ -350,12 +408,35 @@ __global__ void k_prescale(const S* __restrict__ x, const float* __restrict__ di
 // ------------------------------------------------------------------ Eq. 4 layer
 constexpr int kChunk = 8;  // neighbour rows in flight per row group per trip
 
+// tanh of Eq. 4. With fp32 storage: CUDA's tanhf. With bf16 storage the result is
+// rounded to 8 significant bits right after, so the hardware approximation (relative
+// error below 2^-10.9, under a quarter of a bf16 rounding step) is used.
+template <typename S>
+__device__ __forceinline__ float tanh_for(float y);
+template <>
+__device__ __forceinline__ float tanh_for<float>(float y) {
+  return tanhf(y);
+}
+template <>
+__device__ __forceinline__ float tanh_for<__nv_bfloat16>(float y) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(y));
+  return t;
+}
+
 template <typename S>
 struct Raw;
 template <>
 struct Raw<float> {
   using T = float4;
   static __device__ __forceinline__ float4 load(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+  static __device__ __forceinline__ float4 load_pol(const float* p, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+  }
   static __device__ __forceinline__ float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
   static __device__ __forceinline__ void add(float (&a)[4], float4 x) {
     a[0] += x.x; a[1] += x.y; a[2] += x.z; a[3] += x.w;
@@ -368,10 +449,27 @@ template <>
 struct Raw<__nv_bfloat16> {
   using T = uint4;
   static __device__ __forceinline__ uint4 load(const __nv_bfloat16* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
+  static __device__ __forceinline__ uint4 load_pol(const __nv_bfloat16* p, uint64_t pol) {
+    uint4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+  }
   static __device__ __forceinline__ uint4 zero() { return make_uint4(0u, 0u, 0u, 0u); }
+  // a[2k] += low bf16 of word k, a[2k+1] += high bf16, each one mixed-precision add
+  // (bf16 operand, fp32 accumulator and result; the same value as converting first).
+  static __device__ __forceinline__ void add2(float& lo, float& hi, uint32_t w) {
+    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\tadd.rn.f32.bf16 %0, l, %0;\n\t"
+        "add.rn.f32.bf16 %1, h, %1;\n\t}"
+        : "+f"(lo), "+f"(hi)
+        : "r"(w));
+  }
   static __device__ __forceinline__ void add(float (&a)[8], uint4 x) {
-    a[0] += bf_lo(x.x); a[1] += bf_hi(x.x); a[2] += bf_lo(x.y); a[3] += bf_hi(x.y);
-    a[4] += bf_lo(x.z); a[5] += bf_hi(x.z); a[6] += bf_lo(x.w); a[7] += bf_hi(x.w);
+    add2(a[0], a[1], x.x);
+    add2(a[2], a[3], x.y);
+    add2(a[4], a[5], x.z);
+    add2(a[6], a[7], x.w);
   }
   static __device__ __forceinline__ void unpack(uint4 x, float (&v)[8]) {
     v[0] = bf_lo(x.x); v[1] = bf_hi(x.x); v[2] = bf_lo(x.y); v[3] = bf_hi(x.y);
@@ -390,15 +488,16 @@ constexpr float kQScale = 1073741824.0f;  // 2^30
 // Chunks are independent (tanh and the column statistics act per column); each has
 // its own partials and ticket.
 //
-// Rows are taken in `perm` order (decreasing degree) in tiles of GPW rows, one row per
-// group of G lanes; as the rows of a tile have (nearly) equal degree, the groups of a
-// warp run their gather loops in lockstep.
+// Rows are taken in their own order in warp tiles of GPW consecutive rows, one row per
+// group of G lanes. On the degree-relabelled graph the rows of a tile have (nearly)
+// equal degree, so the groups run their gather loops in lockstep. Rows below `hot` are
+// gathered with an evict-last L2 policy and the others evict-first.
 template <int D, typename S>
 __global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const float* __restrict__ dinv,
-    const float* __restrict__ wsum, const int32_t* __restrict__ perm, const S* __restrict__ Tin_all,
-    S* __restrict__ Tout_all, const float* __restrict__ stats_in, long long* __restrict__ partials_all,
-    float* __restrict__ stats_out, unsigned* __restrict__ tickets, int32_t N, int32_t d, float alpha, float theta,
+    const float* __restrict__ wsum, const S* __restrict__ Tin_all, S* __restrict__ Tout_all,
+    const float* __restrict__ stats_in, long long* __restrict__ partials_all, float* __restrict__ stats_out,
+    unsigned* __restrict__ tickets, int32_t N, int32_t d, int32_t hot, int hints, float alpha, float theta,
     int ddof) {
   using RW = Raw<S>;
   using RT = typename RW::T;
@@ -426,7 +525,9 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
     s_is[c] = stats_in ? stats_in[d + c0 + c] : 1.0f;
   }
   __syncthreads();
-  const uint64_t pol = evict_first_policy();
+  const uint64_t pol_first = evict_first_policy();
+  const uint64_t pol_last = hints ? evict_last_policy() : evict_normal_policy();
+  const uint64_t pol_cold = hints ? pol_first : pol_last;
 
   long long qs[VPL], qq[VPL];
 #pragma unroll
@@ -436,16 +537,12 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
   const int64_t nw = (int64_t)gridDim.x * kLayerWarps;
   const int64_t w0 = (int64_t)blockIdx.x * kLayerWarps + warp;
 
-  auto perm_at = [&](int64_t tile) -> int {
-    const int64_t p = tile * GPW + grp;
-    return (tile < ntiles && p < N) ? __ldg(perm + p) : -1;
-  };
   // lane lig holds trip entries lig + G k (k < IPL) counted from `base`, below `end`
   auto load_idx = [&](int (&jw)[IPL], int base, int end) {
 #pragma unroll
     for (int k = 0; k < IPL; ++k) {
       const int t = lig + G * k;
-      jw[k] = (t < C && base + t < end) ? ld_stream(col + base + t, pol) : 0;
+      jw[k] = (t < C && base + t < end) ? ld_stream(col + base + t, pol_first) : 0;
     }
   };
   struct RowData {
@@ -453,11 +550,12 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
     RT self;
     float di, wi;
   };
-  auto fetch_row = [&](int r, RowData& rd) {
-    if (r >= 0) {
+  auto fetch_row = [&](int64_t tile, RowData& rd) {
+    const int64_t r = tile * GPW + grp;
+    if (tile < ntiles && r < N) {
       rd.b = __ldg(row_ptr + r);
       rd.e = __ldg(row_ptr + r + 1);
-      rd.self = RW::load(Tin + (int64_t)r * D);
+      rd.self = RW::load(Tin + r * D);
       rd.di = __ldg(dinv + r);
       rd.wi = __ldg(wsum + r);
     } else {
@@ -467,17 +565,15 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
     }
   };
 
-  // three-stage pipeline over tiles: perm (t+2), row data (t+1), gathers (t)
-  int r = perm_at(w0);
+  // two-stage pipeline over tiles: row data (t+1) while gathering tile t
   RowData cur;
-  fetch_row(r, cur);
-  int r_n = perm_at(w0 + nw);
+  fetch_row(w0, cur);
   int jw[IPL];
   load_idx(jw, cur.b, cur.e);
   for (int64_t tile = w0; tile < ntiles; tile += nw) {
-    const int r_nn = perm_at(tile + 2 * nw);
+    const int64_t r = tile * GPW + grp;
     RowData nxt;
-    fetch_row(r_n, nxt);
+    fetch_row(tile + nw, nxt);
 
     const int ntrip = (cur.e - cur.b + C - 1) / C;
     const int mtrip = __reduce_max_sync(0xffffffffu, ntrip);
@@ -492,7 +588,7 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
 #pragma unroll
       for (int t = 0; t < C; ++t) {
         const int j = __shfl_sync(0xffffffffu, jw[t / G], t % G, G);
-        x[t] = (c + t < cur.e) ? RW::load(Tin + (int64_t)j * D) : RW::zero();
+        x[t] = (c + t < cur.e) ? RW::load_pol(Tin + (int64_t)j * D, j < hot ? pol_last : pol_cold) : RW::zero();
       }
 #pragma unroll
       for (int t = 0; t < C; ++t) RW::add(acc, x[t]);
@@ -501,7 +597,7 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
     }
     // first trip indices of the next tile, then this tile's epilogue
     load_idx(jw, nxt.b, nxt.e);
-    if (r >= 0) {
+    if (r < N) {
       float sv[VPL];
       RW::unpack(cur.self, sv);
       const bool scaled = cur.di > 0.0f;
@@ -515,15 +611,16 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
         const float zi = (ti - mu) * is;
         const float agg = is * fmaf(-mu, cur.wi, acc[v]);
         const float y = fmaf(theta, zi, alpha * cur.di * agg);
-        const float t = tanhf(y);
+        const float t = tanh_for<S>(y);
         qs[v] += __float2ll_rn(t * kQScale);
         qq[v] += __float2ll_rn(t * t * kQScale);
         o[v] = scaled ? cur.di * t : t;
       }
-      store_chunk_cs(Tout + (int64_t)r * D, o);
+      if (r < hot)
+        store_chunk(Tout + r * D, o);
+      else
+        store_chunk_cs(Tout + r * D, o);
     }
-    r = r_n;
-    r_n = r_nn;
     cur = nxt;
   }
 
@@ -589,7 +686,8 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
 // ------------------------------------------------------------------ output
 template <int D, typename S>
 __global__ void k_output(const S* __restrict__ T, const float* __restrict__ dinv, const float* __restrict__ stats,
-                         int32_t N, int32_t dc, int row_l2, float* __restrict__ out) {
+                         const int32_t* __restrict__ rowid, int32_t N, int32_t dc, int row_l2,
+                         float* __restrict__ out) {
   constexpr int VPL = Store<S>::VPL;
   constexpr int G = D / VPL;  // lanes per row
   constexpr int RPW = 32 / G;  // rows per warp pass
@@ -628,7 +726,7 @@ __global__ void k_output(const S* __restrict__ T, const float* __restrict__ dinv
       for (int e = 0; e < VPL; ++e) o[e] *= inv;
     }
     if (ok) {
-      float* p = out + i * D + chunk * VPL;
+      float* p = out + (rowid ? (int64_t)__ldg(rowid + i) : i) * D + chunk * VPL;  // original row
 #pragma unroll
       for (int e = 0; e < VPL; e += 4)
         *reinterpret_cast<float4*>(p + e) = make_float4(o[e], o[e + 1], o[e + 2], o[e + 3]);
@@ -651,7 +749,7 @@ struct LayerCfg {
   static constexpr int GPW = 32 / (D / Store<S>::VPL);
   // CTAs per chunk: one full wave, or fewer for small graphs
   static int grid(int32_t N) {
-      const int64_t rows_per_cta = (int64_t)kLayerWarps * GPW;
+    const int64_t rows_per_cta = (int64_t)kLayerWarps * GPW;
     const int64_t want = ((int64_t)N + rows_per_cta - 1) / rows_per_cta;
     const int64_t cap = (int64_t)per_sm() * num_sms();
     return (int)std::max<int64_t>(1, std::min(want, cap));
@@ -659,40 +757,39 @@ struct LayerCfg {
 };
 
 template <int D, typename S>
-igp_status layer_launch(const igp_graph* g, const void* Tin, void* Tout, const float* st_in, long long* partials,
-                        float* st_out, unsigned* tickets, float alpha, float theta, int ddof, int grid, int d,
-                        cudaStream_t s) {
-  dim3 gr(grid, d / D);
-  k_layer<D, S><<<gr, kLayerThreads, 0, s>>>(g->row_ptr, g->col, g->dinv, g->wsum, g->perm, (const S*)Tin, (S*)Tout,
-                                             st_in, partials, st_out, tickets, g->N, d, alpha, theta, ddof);
+igp_status layer_launch(const LayerArgs& a, cudaStream_t s) {
+  dim3 gr(a.grid, a.d / D);
+  k_layer<D, S><<<gr, kLayerThreads, 0, s>>>(a.row_ptr, a.col, a.dinv, a.wsum, (const S*)a.Tin, (S*)a.Tout,
+                                             a.stats_in, a.partials, a.stats_out, a.tickets, a.N, a.d, a.hot,
+                                             a.hints, a.alpha, a.theta, a.ddof);
   return after_launch("k_layer");
 }
 
 template <int D, typename S>
-igp_status output_launch(const void* T, const float* dinv, const float* st, int32_t N, int dc, int row_l2, float* out,
-                         cudaStream_t s) {
+igp_status output_launch(const void* T, const float* dinv, const float* st, const int32_t* rowid, int32_t N, int dc,
+                         int row_l2, float* out, cudaStream_t s) {
   constexpr int G = D / Store<S>::VPL;
   int64_t threads = (int64_t)N * G;
   int blocks = (int)std::min<int64_t>((threads + 255) / 256, (int64_t)num_sms() * 16);
-  k_output<D, S><<<std::max(blocks, 1), 256, 0, s>>>((const S*)T, dinv, st, N, dc, row_l2, out);
+  k_output<D, S><<<std::max(blocks, 1), 256, 0, s>>>((const S*)T, dinv, st, rowid, N, dc, row_l2, out);
   return after_launch("k_output");
 }
 
 template <typename S>
-igp_status prescale_launch(const void* x, const float* dinv, int32_t N, int32_t d, int32_t dc, void* out,
-                           cudaStream_t s) {
+igp_status prescale_launch(const void* x, const float* dinv, const int32_t* rowid, int32_t N, int32_t d, int32_t dc,
+                           void* out, cudaStream_t s) {
   int64_t total = (int64_t)N * d / Store<S>::VPL;
   int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms() * 16);
-  k_prescale<S><<<std::max(blocks, 1), 256, 0, s>>>((const S*)x, dinv, N, d, dc, (S*)out);
+  k_prescale<S><<<std::max(blocks, 1), 256, 0, s>>>((const S*)x, dinv, rowid, N, d, dc, (S*)out);
   return after_launch("k_prescale");
 }
 
 struct Ops {
   int (*grid)(int32_t);
-  igp_status (*layer)(const igp_graph*, const void*, void*, const float*, long long*, float*, unsigned*, float, float,
-                      int, int, int, cudaStream_t);
-  igp_status (*output)(const void*, const float*, const float*, int32_t, int, int, float*, cudaStream_t);
-  igp_status (*prescale)(const void*, const float*, int32_t, int32_t, int32_t, void*, cudaStream_t);
+  igp_status (*layer)(const LayerArgs&, cudaStream_t);
+  igp_status (*output)(const void*, const float*, const float*, const int32_t*, int32_t, int, int, float*,
+                       cudaStream_t);
+  igp_status (*prescale)(const void*, const float*, const int32_t*, int32_t, int32_t, int32_t, void*, cudaStream_t);
 };
 
 template <int D, typename S>
@@ -702,6 +799,8 @@ Ops ops_for() {
 
 // L2 budget for the gathered chunk of T^(l-1): chunks of at most this many bytes.
 constexpr size_t kChunkBytes = 72ull << 20;
+// Share of L2 given to the most-gathered rows (evict-last); the rest is for streams.
+constexpr size_t kHotBytes = 48ull << 20;
 
 // Column chunk width for a layer: the widest of d, d/2, d/4, .. whose N x width slice
 // fits the L2 budget, but never below 128 bytes per row: a gathered row segment is then
@@ -711,6 +810,14 @@ int chunk_width(int32_t N, int d, size_t sb) {
   int w = d;
   while ((size_t)N * w * sb > kChunkBytes && w * sb > 128) w >>= 1;
   return w;
+}
+
+// Number of leading (highest-degree) rows gathered with the evict-last policy
+// (hot_bytes 0: the default share; negative: no L2 priority hints at all).
+int32_t hot_rows(int32_t N, int dc, size_t sb, int64_t hot_bytes) {
+  if (hot_bytes < 0) return 0;
+  const int64_t hb = hot_bytes > 0 ? hot_bytes : (int64_t)kHotBytes;
+  return (int32_t)std::min<int64_t>(N, hb / ((int64_t)dc * (int64_t)sb));
 }
 
 bool get_ops(int d, int storage, Ops* o) {
@@ -725,47 +832,97 @@ bool get_ops(int d, int storage, Ops* o) {
   }
 }
 
+igp_status launch_dinv_wsum(const int32_t* row_ptr, const int32_t* col, int32_t N, double tau, double eps,
+                            float* dinv, float* wsum, cudaStream_t s) {
+  int blocks = (int)std::min<int64_t>(((int64_t)N + 255) / 256, (int64_t)num_sms() * 8);
+  k_dinv<<<std::max(blocks, 1), 256, 0, s>>>(row_ptr, N, tau, eps, dinv);
+  IGP_TRY(after_launch("k_dinv"));
+  int wblocks = (int)std::min<int64_t>(((int64_t)N * 32 + 255) / 256, (int64_t)num_sms() * 16);
+  k_wsum<<<std::max(wblocks, 1), 256, 0, s>>>(row_ptr, col, dinv, N, wsum);
+  return after_launch("k_wsum");
+}
+
 }  // namespace
 
-igp_status ensure_perm(igp_graph* g, cudaStream_t s) {
-  if (g->perm) return IGP_OK;
+// Rows by decreasing degree (g->perm), its inverse and the relabelled CSR, once per graph.
+igp_status ensure_layer_csr(igp_graph* g, cudaStream_t s) {
+  if (g->lcol) return IGP_OK;
   const int32_t N = g->N;
   const int64_t nb = (int64_t)g->max_deg + 1;
+  const int64_t n1 = (int64_t)N + 1;
+  // owned block: perm[N] | inv[N] | lrow_ptr[N+1]; lcol separately
   void* p = nullptr;
-  IGP_TRY(dev_alloc(&p, (size_t)N * sizeof(int32_t), s));
-  g->perm = (int32_t*)p;
+  IGP_TRY(dev_alloc(&p, (size_t)(3 * (int64_t)N + 1) * sizeof(int32_t), s));
+  int32_t* perm = (int32_t*)p;
+  int32_t* inv = perm + N;
+  int32_t* lrow_ptr = inv + N;
+  void* lc = nullptr;
+  igp_status st = dev_alloc(&lc, (size_t)std::max<int64_t>(g->nnz, 1) * sizeof(int32_t), s);
+  if (st != IGP_OK) {
+    dev_free(p, s);
+    return st;
+  }
+  int32_t* lcol = (int32_t*)lc;
+  // temporaries: hist | off | cur (nb + 1 each) | cnt (N + 1) | scan tiles
+  const int64_t m = std::max<int64_t>(nb + 1, n1);
+  const int64_t ntiles = (m + 8191) / 8192;
   void* t = nullptr;
-  const int64_t ntiles = (nb + 1 + 8191) / 8192;
-  IGP_TRY(dev_alloc(&t, (size_t)(3 * (nb + 1) + ntiles) * sizeof(int), s));
+  st = dev_alloc(&t, (size_t)(3 * (nb + 1) + n1 + ntiles) * sizeof(int), s);
+  if (st != IGP_OK) {
+    dev_free(lc, s);
+    dev_free(p, s);
+    return st;
+  }
   int* hist = (int*)t;
   int* off = hist + (nb + 1);
   int* cur = off + (nb + 1);
-  int* tmp = cur + (nb + 1);
-  igp_status st = IGP_OK;
+  int* cnt = cur + (nb + 1);
+  int* tmp = cnt + n1;
   if (cudaMemsetAsync(hist, 0, (nb + 1) * sizeof(int), s) != cudaSuccess ||
       cudaMemsetAsync(cur, 0, (nb + 1) * sizeof(int), s) != cudaSuccess)
     st = cuda_status(cudaGetLastError(), "memset", __FILE__, __LINE__);
-  const int blocks = (int)(((int64_t)N + kPermRowsPerBlock - 1) / kPermRowsPerBlock);
+  const int pblocks = (int)(((int64_t)N + kPermRowsPerBlock - 1) / kPermRowsPerBlock);
   const size_t smem = nb <= kPermSmemBins ? (size_t)nb * sizeof(int) : 0;
+  const int blocks = (int)std::min<int64_t>((n1 + 255) / 256, (int64_t)num_sms() * 8);
+  const int wblocks = (int)std::min<int64_t>(((int64_t)N * 32 + 255) / 256, (int64_t)num_sms() * 16);
   if (st == IGP_OK) {
-    k_deg_hist<<<blocks, 512, smem, s>>>(g->row_ptr, N, g->max_deg, hist);
+    k_deg_hist<<<pblocks, 512, smem, s>>>(g->row_ptr, N, g->max_deg, hist);
     st = after_launch("k_deg_hist");
   }
   if (st == IGP_OK) st = exclusive_scan(hist, off, nb + 1, tmp, s);
   if (st == IGP_OK) {
-    k_deg_scatter<<<blocks, 512, smem, s>>>(g->row_ptr, N, g->max_deg, off, cur, g->perm);
+    k_deg_scatter<<<pblocks, 512, smem, s>>>(g->row_ptr, N, g->max_deg, off, cur, perm);
     st = after_launch("k_deg_scatter");
+  }
+  if (st == IGP_OK) {
+    k_invert<<<std::max(blocks, 1), 256, 0, s>>>(perm, N, inv);
+    st = after_launch("k_invert");
+  }
+  if (st == IGP_OK) {
+    k_lrow_count<<<std::max(blocks, 1), 256, 0, s>>>(g->row_ptr, perm, N, cnt);
+    st = after_launch("k_lrow_count");
+  }
+  if (st == IGP_OK) st = exclusive_scan(cnt, lrow_ptr, n1, tmp, s);
+  if (st == IGP_OK) {
+    k_relabel<<<std::max(wblocks, 1), 256, 0, s>>>(g->row_ptr, g->col, perm, inv, lrow_ptr, N, lcol);
+    st = after_launch("k_relabel");
   }
   dev_free(t, s);
   if (st != IGP_OK) {
-    dev_free(g->perm, s);
-    g->perm = nullptr;
+    dev_free(lc, s);
+    dev_free(p, s);
+    return st;
   }
-  return st;
+  g->perm = perm;
+  g->inv = inv;
+  g->lrow_ptr = lrow_ptr;
+  g->lcol = lcol;
+  return IGP_OK;
 }
 
 igp_status compute_dinv(igp_graph* g, double tau, double eps, cudaStream_t s, Profile* prof) {
   if (g->dinv_valid && g->dinv_tau == tau && g->dinv_eps == eps) return IGP_OK;
+  IGP_TRY(ensure_layer_csr(g, s));
   if (!g->dinv) {
     void* p = nullptr;
     IGP_TRY(dev_alloc(&p, (size_t)g->N * 2 * sizeof(float), s));
@@ -773,27 +930,28 @@ igp_status compute_dinv(igp_graph* g, double tau, double eps, cudaStream_t s, Pr
     g->wsum = g->dinv + g->N;
   }
   PhaseTimer pt(prof, IGP_PHASE_DINV, s);
-  int blocks = (int)std::min<int64_t>(((int64_t)g->N + 255) / 256, (int64_t)num_sms() * 8);
-  k_dinv<<<std::max(blocks, 1), 256, 0, s>>>(g->row_ptr, g->N, tau, eps, g->dinv);
-  IGP_TRY(after_launch("k_dinv"));
-  int wblocks = (int)std::min<int64_t>(((int64_t)g->N * 32 + 255) / 256, (int64_t)num_sms() * 16);
-  k_wsum<<<std::max(wblocks, 1), 256, 0, s>>>(g->row_ptr, g->col, g->dinv, g->N, g->wsum);
-  IGP_TRY(after_launch("k_wsum"));
+  IGP_TRY(launch_dinv_wsum(g->lrow_ptr, g->lcol, g->N, tau, eps, g->dinv, g->wsum, s));
   g->dinv_valid = true;
   g->dinv_tau = tau;
   g->dinv_eps = eps;
   return IGP_OK;
 }
 
+igp_status dinv_original_order(igp_graph* g, float* out, cudaStream_t s) {
+  int blocks = (int)std::min<int64_t>(((int64_t)g->N + 255) / 256, (int64_t)num_sms() * 8);
+  k_gather_f32<<<std::max(blocks, 1), 256, 0, s>>>(g->dinv, g->inv, g->N, out);
+  return after_launch("k_gather_f32");
+}
+
 igp_status launch_theta(uint64_t seed, int32_t N, int32_t d, int32_t dc, float xs, int storage, const float* dinv,
-                        void* out, cudaStream_t s) {
+                        const int32_t* rowid, void* out, cudaStream_t s) {
   int64_t total = (int64_t)N * (d / 8);
   int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms() * 16);
   blocks = std::max(blocks, 1);
   if (storage == IGP_STORE_BF16)
-    k_theta<__nv_bfloat16><<<blocks, 256, 0, s>>>(seed, N, d, dc, xs, dinv, (__nv_bfloat16*)out);
+    k_theta<__nv_bfloat16><<<blocks, 256, 0, s>>>(seed, N, d, dc, xs, dinv, rowid, (__nv_bfloat16*)out);
   else
-    k_theta<float><<<blocks, 256, 0, s>>>(seed, N, d, dc, xs, dinv, (float*)out);
+    k_theta<float><<<blocks, 256, 0, s>>>(seed, N, d, dc, xs, dinv, rowid, (float*)out);
   return after_launch("k_theta");
 }
 
@@ -809,9 +967,8 @@ igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed
     return IGP_E_INVAL;
   }
   const int nchunks = d / dc;
-  IGP_TRY(compute_dinv(g, tau, o.eps, s, prof));
+  IGP_TRY(compute_dinv(g, tau, o.eps, s, prof));  // also builds the relabelled CSR
   const int grid = lops.grid(N);
-  IGP_TRY(ensure_perm(g, s));
   // workspace: T0 | T1 | stats[2][2d] | partials[nchunks][grid][2dc] | tickets[nchunks]
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t bT = al((size_t)N * d * sb);
@@ -839,25 +996,43 @@ igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed
   {
     PhaseTimer pt(prof, IGP_PHASE_THETA, s);
     if (o.x_in) {
-      IGP_TRY(ops.prescale(o.x_in, g->dinv, N, d, dc, T0, s));
+      IGP_TRY(ops.prescale(o.x_in, g->dinv, g->perm, N, d, dc, T0, s));
     } else {
       const double xs = o.x_scale > 0 ? o.x_scale : 1.0 / std::sqrt((double)d);
-      IGP_TRY(launch_theta(seed, N, d, dc, (float)xs, o.storage, g->dinv, T0, s));
+      IGP_TRY(launch_theta(seed, N, d, dc, (float)xs, o.storage, g->dinv, g->perm, T0, s));
     }
   }
+  LayerArgs la;
+  la.row_ptr = g->lrow_ptr;
+  la.col = g->lcol;
+  la.dinv = g->dinv;
+  la.wsum = g->wsum;
+  la.partials = partials;
+  la.tickets = tickets;
+  la.N = N;
+  la.d = d;
+  la.hot = hot_rows(N, dc, sb, o.l2_hot_bytes);
+  la.hints = o.l2_hot_bytes < 0 ? 0 : 1;
+  la.alpha = (float)o.alpha;
+  la.theta = (float)o.theta;
+  la.ddof = o.znorm_ddof;
+  la.grid = grid;
   const void* cur = T0;
   const float* st_prev = nullptr;
   for (int32_t l = 1; l <= L; ++l) {
     void* dst = (cur == T0) ? T1 : T0;
     float* st = stats + (size_t)(l & 1) * 2 * d;
+    la.Tin = cur;
+    la.Tout = dst;
+    la.stats_in = st_prev;
+    la.stats_out = st;
     PhaseTimer pt(prof, IGP_PHASE_LAYER, s);
-    IGP_TRY(lops.layer(g, cur, dst, st_prev, partials, st, tickets, (float)o.alpha, (float)o.theta, o.znorm_ddof,
-                       grid, d, s));
+    IGP_TRY(lops.layer(la, s));
     cur = dst;
     st_prev = st;
   }
   PhaseTimer pt(prof, IGP_PHASE_OUTPUT, s);
-  return ops.output(cur, g->dinv, st_prev, N, dc, o.out_row_l2, out_dev, s);
+  return ops.output(cur, g->dinv, st_prev, g->perm, N, dc, o.out_row_l2, out_dev, s);
 }
 
 }  // namespace igp
@@ -883,11 +1058,6 @@ namespace {
 
 constexpr size_t kNoAllocScratchBytes = 16ull << 20;  // 16 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-
-__global__ void k_iota(int32_t N, int32_t* __restrict__ out) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = (int32_t)i;
-}
 
 // Device address of g_noalloc_scratch on the current device (host code may not use the
 // symbol itself: on the host it names a stand-in, not device memory).
@@ -948,7 +1118,7 @@ extern "C" igp_status igp_embed_noalloc(const int32_t* row_ptr, const int32_t* c
     set_error("igp_embed_noalloc: row_ptr, col, out (and opts->x_in) must be device memory");
     return IGP_E_INVAL;
   }
-  // scratch layout: dinv | w | perm | T0 | T1 | stats[2][2d] | partials[grid][2d] | ticket
+  // scratch layout: dinv | w | T0 | T1 | stats[2][2d] | partials[grid][2d] | ticket
   const size_t sb = o.storage == IGP_STORE_BF16 ? 2 : 4;
   const int grid = ops.grid(N);
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -956,7 +1126,7 @@ extern "C" igp_status igp_embed_noalloc(const int32_t* row_ptr, const int32_t* c
   const size_t bT = al((size_t)N * d * sb);
   const size_t bS = al(2 * 2 * (size_t)d * sizeof(float));
   const size_t bP = al((size_t)grid * 2 * d * sizeof(long long));
-  const size_t need = 3 * bN + 2 * bT + bS + bP + 256;
+  const size_t need = 2 * bN + 2 * bT + bS + bP + 256;
   if (need > kNoAllocScratchBytes) {
     set_error("igp_embed_noalloc: N=%d, d=%d needs %zu bytes of scratch, more than the fixed %zu (16 MiB); "
               "use igp_embed for this size",
@@ -967,40 +1137,50 @@ extern "C" igp_status igp_embed_noalloc(const int32_t* row_ptr, const int32_t* c
   IGP_TRY(noalloc_scratch(&scratch));
   cudaStream_t s = (cudaStream_t)stream;
   char* base = (char*)scratch;
-  // a non-owning view of the caller's CSR with the scratch-resident per-graph arrays
-  igp_graph gv;
-  gv.N = N;
-  gv.row_ptr = const_cast<int32_t*>(row_ptr);
-  gv.col = const_cast<int32_t*>(col);
-  gv.dinv = (float*)base;
-  gv.wsum = (float*)(base + bN);
-  gv.perm = (int32_t*)(base + 2 * bN);
-  void* T0 = base + 3 * bN;
-  void* T1 = base + 3 * bN + bT;
-  float* stats = (float*)(base + 3 * bN + 2 * bT);
-  long long* partials = (long long*)(base + 3 * bN + 2 * bT + bS);
-  unsigned* ticket = (unsigned*)(base + 3 * bN + 2 * bT + bS + bP);
+  float* dinv = (float*)base;
+  float* wsum = (float*)(base + bN);
+  void* T0 = base + 2 * bN;
+  void* T1 = base + 2 * bN + bT;
+  float* stats = (float*)(base + 2 * bN + 2 * bT);
+  long long* partials = (long long*)(base + 2 * bN + 2 * bT + bS);
+  unsigned* ticket = (unsigned*)(base + 2 * bN + 2 * bT + bS + bP);
   IGP_TRY_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s));
 
-  IGP_TRY(compute_dinv(&gv, tau, o.eps, s, nullptr));  // writes dinv and w in place
-  const int blocks = (int)std::min<int64_t>(((int64_t)N + 255) / 256, (int64_t)num_sms() * 8);
-  k_iota<<<std::max(blocks, 1), 256, 0, s>>>(N, gv.perm);  // rows in their own order
-  IGP_TRY(after_launch("k_iota"));
+  // the caller's graph as it is (no relabelling: that would need memory)
+  IGP_TRY(launch_dinv_wsum(row_ptr, col, N, tau, o.eps, dinv, wsum, s));
   if (o.x_in) {
-    IGP_TRY(ops.prescale(o.x_in, gv.dinv, N, d, d, T0, s));
+    IGP_TRY(ops.prescale(o.x_in, dinv, nullptr, N, d, d, T0, s));
   } else {
     const double xs = o.x_scale > 0 ? o.x_scale : 1.0 / std::sqrt((double)d);
-    IGP_TRY(launch_theta(seed, N, d, d, (float)xs, o.storage, gv.dinv, T0, s));
+    IGP_TRY(launch_theta(seed, N, d, d, (float)xs, o.storage, dinv, nullptr, T0, s));
   }
+  LayerArgs la;
+  la.row_ptr = row_ptr;
+  la.col = col;
+  la.dinv = dinv;
+  la.wsum = wsum;
+  la.partials = partials;
+  la.tickets = ticket;
+  la.N = N;
+  la.d = d;
+  la.hot = hot_rows(N, d, sb, o.l2_hot_bytes);
+  la.hints = o.l2_hot_bytes < 0 ? 0 : 1;
+  la.alpha = (float)o.alpha;
+  la.theta = (float)o.theta;
+  la.ddof = o.znorm_ddof;
+  la.grid = grid;
   const void* cur = T0;
   const float* st_prev = nullptr;
   for (int32_t l = 1; l <= L; ++l) {
     void* dst = (cur == T0) ? T1 : T0;
     float* st = stats + (size_t)(l & 1) * 2 * d;
-    IGP_TRY(ops.layer(&gv, cur, dst, st_prev, partials, st, ticket, (float)o.alpha, (float)o.theta, o.znorm_ddof,
-                      grid, d, s));
+    la.Tin = cur;
+    la.Tout = dst;
+    la.stats_in = st_prev;
+    la.stats_out = st;
+    IGP_TRY(ops.layer(la, s));
     cur = dst;
     st_prev = st;
   }
-  return ops.output(cur, gv.dinv, st_prev, N, d, o.out_row_l2, out, s);
+  return ops.output(cur, dinv, st_prev, nullptr, N, d, o.out_row_l2, out, s);
 }

@@ -77,8 +77,12 @@ struct igp_graph {
   // Eq. 1 factors for the last (tau, eps) asked for, and w_i = sum_{j in N(i)} dinv_j
   float* dinv = nullptr;       // device [N]
   float* wsum = nullptr;       // device [N], same allocation as dinv
-  // rows in order of decreasing degree (the layer kernel's processing order)
+  // the graph relabelled by decreasing degree ("layer CSR"): layer row k is original row
+  // perm[k]; inv[perm[k]] = k; one allocation holds perm | inv | lrow_ptr
   int32_t* perm = nullptr;
+  int32_t* inv = nullptr;
+  int32_t* lrow_ptr = nullptr;
+  int32_t* lcol = nullptr;
   double dinv_tau = 0, dinv_eps = 0;
   bool dinv_valid = false;
   // FFP workspace (grown on demand, kept until free)
@@ -95,12 +99,35 @@ igp_status exclusive_scan(const int* in, int* out, int64_t n, int* tmp, cudaStre
 // csr_build.cu: CSR of the undirected edge list (device inputs), into g (empty).
 igp_status build_csr(const int32_t* src, const int32_t* dst, int64_t M, int32_t N, cudaStream_t s,
                      igp_graph* g);
+// Arguments of one layer launch.
+struct LayerArgs {
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const float* dinv;
+  const float* wsum;
+  const void* Tin;
+  void* Tout;
+  const float* stats_in;
+  long long* partials;
+  float* stats_out;
+  unsigned* tickets;
+  int32_t N, d, hot;
+  int hints;
+  float alpha, theta;
+  int ddof, grid;
+};
+
 // ffp.cu
+igp_status ensure_layer_csr(igp_graph* g, cudaStream_t s);
+// dinv and w in layer-CSR order, for (tau, eps); builds the layer CSR on first use.
 igp_status compute_dinv(igp_graph* g, double tau, double eps, cudaStream_t s, Profile* prof);
+// g's dinv (layer order) written in original node order into `out` (device).
+igp_status dinv_original_order(igp_graph* g, float* out, cudaStream_t s);
 // Theta (Alg. 1, line 2) into `out` in the storage type, in column blocks of dc columns
-// (dc = d: row-major), multiplied row-wise by dinv if non-NULL.
+// (dc = d: row-major), multiplied row-wise by dinv if non-NULL; row i holds the draw of
+// node rowid[i] (rowid NULL: node i).
 igp_status launch_theta(uint64_t seed, int32_t N, int32_t d, int32_t dc, float x_scale, int storage,
-                        const float* dinv, void* out, cudaStream_t s);
+                        const float* dinv, const int32_t* rowid, void* out, cudaStream_t s);
 igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed, float* out_dev,
                    const igp_embed_opts& o, cudaStream_t s);
 }  // namespace igp
