@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--chunk-cols", type=int, default=0, help="columns per layer pass (0: automatic)")
-    p.add_argument("--l2-hot-bytes", type=int, default=0, help="L2 share for hot rows (0: default, <0: no hints)")
+    p.add_argument("--gather", default="auto", choices=["auto", "lsu", "bulk", "tma4"])
     return p.parse_args()
 
 
@@ -239,7 +239,7 @@ def main():
     dst = torch.from_numpy(g.dst).cuda()
     out = torch.empty((N, d), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    opts = api.embed_opts(storage=storage, chunk_cols=args.chunk_cols, l2_hot_bytes=args.l2_hot_bytes)
+    opts = api.embed_opts(storage=storage, chunk_cols=args.chunk_cols, gather=args.gather)
     probe = api.graph_build(src, dst, N)
     _, nnz, maxdeg = probe.info()
     probe.free()
@@ -341,7 +341,8 @@ def main():
         "vs_baseline": None, "dtype": storage, "data": "synthetic",
         "config": {"workload": args.workload, **wl["graph"], "M_drawn": M, "nnz": int(nnz), "max_deg": int(maxdeg),
                    "d": d, "tau": tau, "L": L, "storage": storage, "accumulate": "f32",
-                   "chunk_cols": args.chunk_cols or "auto", "l2_hot_bytes": args.l2_hot_bytes or "auto",
+                   "chunk_cols": args.chunk_cols or "auto",
+                   "gather": args.gather,
                    "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (edge list %d MB, T %d MB each > 129 MB)" % (
                        8 * M >> 20, N * d * sb >> 20) if N * d * sb > L2_BYTES else "working set may fit L2"},

@@ -54,6 +54,12 @@ typedef int32_t igp_status;
 #define IGP_STORE_F32  0
 #define IGP_STORE_BF16 1
 
+/* How a layer brings neighbour rows to the SM (igp_embed_opts.gather). Result-neutral. */
+#define IGP_GATHER_AUTO 0  /* the measured best (currently register loads for every width) */
+#define IGP_GATHER_LSU  1  /* 16-byte register loads by the lanes of each row group */
+#define IGP_GATHER_BULK 2  /* one cp.async.bulk copy per row into a per-warp shared-memory ring */
+#define IGP_GATHER_TMA4 3  /* cp.async.bulk.tensor tile::gather4 (4 rows per copy); needs chunk_cols 0 */
+
 /* Phases timed by an igp_profile (device time between CUDA events). */
 #define IGP_PHASE_DINV   0  /* Eq. 1 degree factors (fp64 on the device) */
 #define IGP_PHASE_THETA  1  /* Theta generation (Alg. 1, line 2) */
@@ -78,9 +84,8 @@ typedef struct igp_embed_opts {
                           whose N x width slice of the activations fits ~72 MB of L2, keeping at
                           least 128 bytes per row. Otherwise a power of two dividing d, >= 8, with
                           at least 16 bytes per row. Result-neutral (exact integer statistics). */
-  int64_t l2_hot_bytes;/* L2 share for the most-gathered (highest-degree) activation rows, which a
-                          layer loads with an evict-last policy and the rest evict-first; 0 (default)
-                          = 48 MiB, < 0 = no L2 priority hints. Result-neutral. */
+  int32_t gather;      /* IGP_GATHER_AUTO (default), _LSU, _BULK or _TMA4 */
+  int32_t reserved_test;/* 0. (Non-zero only in the library's own test of its bounded device waits.) */
   const void* x_in;    /* NULL: Theta from `seed`. Else a DEVICE pointer to N x d row-major values in
                           the storage type, used as Z^(0) instead (not modified). */
   igp_profile* profile;/* NULL, or a profile that records per-phase device times of this call */
@@ -125,6 +130,11 @@ igp_status igp_graph_export(const igp_graph* g, int32_t* row_ptr, int32_t* col, 
 /* Eq. 1 degree factors D_tau^{-1/2} as fp32 (computed in fp64, IEEE sqrt and division, then
  * rounded to nearest fp32), dinv[N] host or device. 0 where D_tau == 0 (tau = 0, isolated node). */
 igp_status igp_degree_factors(igp_graph* g, double tau, double eps, float* dinv, void* stream);
+
+/* Wait for all work issued on the handle; IGP_E_TIMEOUT if a device-side wait of the last
+ * igp_embed on it ran out (about a second without progress: its output is then invalid), else
+ * IGP_OK or IGP_E_CUDA. */
+igp_status igp_graph_sync(igp_graph* g);
 
 /* Release a graph and its device memory. NULL is a no-op. The memory is returned to the library's
  * pool in stream order after the last work issued on the handle; the call does not block. */

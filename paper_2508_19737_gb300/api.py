@@ -26,6 +26,12 @@ IGP_E_UNSUPPORTED = 8
 IGP_STORE_F32 = 0
 IGP_STORE_BF16 = 1
 
+IGP_GATHER_AUTO = 0
+IGP_GATHER_LSU = 1
+IGP_GATHER_BULK = 2
+IGP_GATHER_TMA4 = 3
+GATHER = {"auto": IGP_GATHER_AUTO, "lsu": IGP_GATHER_LSU, "bulk": IGP_GATHER_BULK, "tma4": IGP_GATHER_TMA4}
+
 IGP_PHASE_DINV = 0
 IGP_PHASE_THETA = 1
 IGP_PHASE_LAYER = 2
@@ -53,7 +59,8 @@ class EmbedOpts(ctypes.Structure):
         ("storage", ctypes.c_int32),
         ("out_row_l2", ctypes.c_int32),
         ("chunk_cols", ctypes.c_int32),
-        ("l2_hot_bytes", ctypes.c_int64),
+        ("gather", ctypes.c_int32),
+        ("reserved_test", ctypes.c_int32),
         ("x_in", ctypes.c_void_p),
         ("profile", ctypes.c_void_p),
     ]
@@ -77,6 +84,7 @@ _SIGS = {
     "igp_degree_factors": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
                                             ctypes.c_void_p]),
     "igp_graph_free": (None, [ctypes.c_void_p]),
+    "igp_graph_sync": (ctypes.c_int32, [ctypes.c_void_p]),
     "igp_generate_x": (ctypes.c_int32, [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                         ctypes.c_void_p, ctypes.c_void_p]),
     "igp_embed": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
@@ -149,7 +157,7 @@ def launch_count():
 
 
 def embed_opts(alpha=1.0, theta=0.1, eps=1e-3, x_scale=0.0, znorm_ddof=1, storage="f32", out_row_l2=False,
-               x_in=None, profile=None, chunk_cols=0, l2_hot_bytes=0):
+               x_in=None, profile=None, chunk_cols=0, gather="auto", reserved_test=0):
     o = EmbedOpts()
     lib().igp_embed_opts_init(ctypes.byref(o))
     o.alpha, o.theta, o.eps, o.x_scale = alpha, theta, eps, x_scale
@@ -157,7 +165,8 @@ def embed_opts(alpha=1.0, theta=0.1, eps=1e-3, x_scale=0.0, znorm_ddof=1, storag
     o.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
     o.out_row_l2 = 1 if out_row_l2 else 0
     o.chunk_cols = int(chunk_cols)
-    o.l2_hot_bytes = int(l2_hot_bytes)
+    o.gather = GATHER[gather] if isinstance(gather, str) else int(gather)
+    o.reserved_test = int(reserved_test)
     o.x_in = _ptr(x_in)
     o.profile = profile.handle if profile is not None else None
     return o
@@ -218,6 +227,11 @@ class Graph:
             col = np.empty(nnz, dtype=np.int32)
         _check(lib().igp_graph_export(self.handle, _ptr(row_ptr), _ptr(col), _stream(stream)))
         return row_ptr, col
+
+    def sync(self):
+        """igp_graph_sync: wait for the handle's work; raises IgpError(IGP_E_TIMEOUT) if a
+        device-side wait of the last embed ran out."""
+        _check(lib().igp_graph_sync(self.handle))
 
     def free(self):
         if self.handle:

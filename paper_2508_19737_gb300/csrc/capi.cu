@@ -205,11 +205,14 @@ igp_status igp_graph_build_profiled(const int32_t* src, const int32_t* dst, int6
     return IGP_E_NOMEM;
   }
   cudaGetDevice(&g->device);
-  if (cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess) {
-    igp_status e = cuda_status(cudaGetLastError(), "event create", __FILE__, __LINE__);
+  if (cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaHostAlloc((void**)&g->err_host, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+    igp_status e = cuda_status(cudaGetLastError(), "graph handle set-up", __FILE__, __LINE__);
+    if (g->done) cudaEventDestroy(g->done);
     delete g;
     return e;
   }
+  *g->err_host = 0;
   const void *ds = nullptr, *dd = nullptr;
   void *os = nullptr, *od = nullptr;
   igp_status st = to_device(src, (size_t)M * sizeof(int32_t), s, &ds, &os);
@@ -223,6 +226,7 @@ igp_status igp_graph_build_profiled(const int32_t* src, const int32_t* dst, int6
   if (st == IGP_OK) st = graph_mark(g, s);
   if (st != IGP_OK) {
     cudaEventDestroy(g->done);
+    cudaFreeHost(g->err_host);
     delete g;
     return st;
   }
@@ -281,18 +285,7 @@ igp_status igp_degree_factors(igp_graph* g, double tau, double eps, float* dinv,
   cudaStream_t s = (cudaStream_t)stream;
   IGP_TRY(graph_wait(g, s));
   IGP_TRY(compute_dinv(g, tau, eps, s, nullptr));
-  const size_t bytes = (size_t)g->N * sizeof(float);
-  igp_status st;
-  if (is_device_ptr(dinv)) {
-    st = dinv_original_order(g, dinv, s);
-  } else {
-    void* tmp = nullptr;
-    IGP_TRY(dev_alloc(&tmp, bytes, s));
-    st = dinv_original_order(g, (float*)tmp, s);
-    if (st == IGP_OK) st = copy_out(dinv, tmp, bytes, s);
-    dev_free(tmp, s);
-  }
-  if (st != IGP_OK) return st;
+  IGP_TRY(copy_out(dinv, g->dinv, (size_t)g->N * sizeof(float), s));
   return graph_mark(g, s);
 }
 
@@ -307,13 +300,30 @@ void igp_graph_free(igp_graph* g) {
   if (g->row_ptr) cudaFreeAsync(g->row_ptr, s);
   if (g->col) cudaFreeAsync(g->col, s);
   if (g->dinv) cudaFreeAsync(g->dinv, s);
-  if (g->perm) cudaFreeAsync(g->perm, s);  // also holds inv and lrow_ptr
-  if (g->lcol) cudaFreeAsync(g->lcol, s);
+  if (g->perm) cudaFreeAsync(g->perm, s);
   if (g->ws) cudaFreeAsync(g->ws, s);
-  if (g->done) cudaEventDestroy(g->done);
+  if (g->done) {
+    cudaEventSynchronize(g->done);  // the pinned error word may still be written
+    cudaEventDestroy(g->done);
+  }
+  if (g->err_host) cudaFreeHost(g->err_host);
   cudaGetLastError();
   if (cur != g->device) cudaSetDevice(cur);
   delete g;
+}
+
+igp_status igp_graph_sync(igp_graph* g) {
+  clear_error();
+  if (!g) {
+    set_error("igp_graph_sync: NULL graph");
+    return IGP_E_INVAL;
+  }
+  if (g->done) IGP_TRY_CUDA(cudaEventSynchronize(g->done));
+  if (g->err_host && *g->err_host) {
+    set_error("a device-side wait of the last igp_embed ran out; its output is invalid");
+    return IGP_E_TIMEOUT;
+  }
+  return IGP_OK;
 }
 
 igp_status igp_generate_x(uint64_t seed, int32_t N, int32_t d, double x_scale, float* out, void* stream) {
@@ -325,10 +335,10 @@ igp_status igp_generate_x(uint64_t seed, int32_t N, int32_t d, double x_scale, f
   cudaStream_t s = (cudaStream_t)stream;
   const double xs = x_scale > 0 ? x_scale : 1.0 / std::sqrt((double)d);
   const size_t bytes = (size_t)N * d * sizeof(float);
-  if (is_device_ptr(out)) return launch_theta(seed, N, d, d, (float)xs, IGP_STORE_F32, nullptr, nullptr, out, s);
+  if (is_device_ptr(out)) return launch_theta(seed, N, d, d, (float)xs, IGP_STORE_F32, nullptr, out, s);
   void* tmp = nullptr;
   IGP_TRY(dev_alloc(&tmp, bytes, s));
-  igp_status st = launch_theta(seed, N, d, d, (float)xs, IGP_STORE_F32, nullptr, nullptr, tmp, s);
+  igp_status st = launch_theta(seed, N, d, d, (float)xs, IGP_STORE_F32, nullptr, tmp, s);
   if (st == IGP_OK) st = copy_out(out, tmp, bytes, s);
   dev_free(tmp, s);
   return st;
@@ -356,6 +366,10 @@ igp_status igp_embed(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t se
     set_error("igp_embed: d=%d unsupported (8, 16, 32, 64, 128)", d);
     return IGP_E_INVAL;
   }
+  if (o.gather < IGP_GATHER_AUTO || o.gather > IGP_GATHER_TMA4) {
+    set_error("igp_embed: unknown gather mode %d", o.gather);
+    return IGP_E_INVAL;
+  }
   if (o.chunk_cols != 0) {
     const int sb = o.storage == IGP_STORE_BF16 ? 2 : 4;
     const int c = o.chunk_cols;
@@ -378,8 +392,12 @@ igp_status igp_embed(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t se
     void* tmp = nullptr;
     IGP_TRY(dev_alloc(&tmp, bytes, s));
     st = run_ffp(g, tau, L, d, seed, (float*)tmp, o, s);
-    if (st == IGP_OK) st = copy_out(out, tmp, bytes, s);
+    if (st == IGP_OK) st = copy_out(out, tmp, bytes, s);  // synchronises
     dev_free(tmp, s);
+    if (st == IGP_OK && *g->err_host) {
+      set_error("igp_embed: a device-side wait ran out; the output is invalid");
+      st = IGP_E_TIMEOUT;
+    }
   }
   if (st == IGP_OK) st = graph_mark(g, s);
   return st;

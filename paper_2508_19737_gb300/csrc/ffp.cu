@@ -1,40 +1,37 @@
 // The feed-forward propagation (FFP) of InfraredGP, Alg. 1 lines 1-6:
 //   k_dinv        Eq. 1 degree correction D_tau and D_tau^{-1/2} (fp64, rounded to fp32)
 //   k_wsum        w_i = sum_{j in N(i)} dinv_j (fp32), once per graph and tau
-//   k_deg_*, k_invert, k_lrow_count, k_relabel
-//                 the "layer CSR": the graph relabelled by decreasing degree, once per graph
+//   k_deg_*       rows in order of decreasing degree, once per graph
 //   k_theta       Z^(0) = Theta ~ N(0, 1/d): Philox4x64-10 + Box-Muller (Alg. 1, line 2)
 //   k_layer       one Eq. 4 layer: T^(l) = tanh(theta Z + alpha Ahat Z), Z = ZNorm(T^(l-1)),
 //                 fused with the column statistics of T^(l) that the next ZNorm needs
+//   k_layer_tma   the same layer with the neighbour rows brought in by the TMA engine
 //   k_output      Z~ = sigmoid(ZNorm(T^(L))) (Eq. 4), optional row L2 normalisation
 //
-// Storage: row k of every N x d activation buffer holds s_k = dinv_k * t_k (t_k itself
-// when dinv_k = 0, an isolated node at tau = 0). With Z = ZNorm(T) = (T - mu) inv_s,
-//     sum_j dinv_j z_j = inv_s (sum_j s_j - mu w_k),
+// Storage: row i of every N x d activation buffer holds s_i = dinv_i * t_i (t_i itself
+// when dinv_i = 0, an isolated node at tau = 0). With Z = ZNorm(T) = (T - mu) inv_s,
+//     sum_j dinv_j z_j = inv_s (sum_j s_j - mu w_i),
 // so a layer gathers neighbour rows and only adds them: no per-neighbour degree
-// factor, no per-neighbour normalisation; the self term uses t_k = s_k / dinv_k.
-//
-// Relabelling: the layers run on the graph with its nodes renumbered by decreasing
-// degree (the FFP commutes with a relabelling; Theta is still drawn for the original
-// ids and the output is written back to the original rows). Then a warp's consecutive
-// rows have (nearly) equal degree, all per-row data is read and written sequentially,
-// and the most-gathered rows are the lowest ids.
+// factor, no per-neighbour normalisation; the self term uses t_i = s_i / dinv_i.
 //
 // Layer kernel (bandwidth-bound sparse gather, no tensor cores):
 //   * a group of G lanes owns one row; each lane owns 16 bytes of it (8 bf16 or 4 fp32
-//     values), so a neighbour row is G coalesced 16-byte loads; a warp takes tiles of
-//     32/G consecutive rows, so its groups have equal trip counts and stay converged;
+//     values), so a neighbour row is G coalesced 16-byte loads;
+//   * rows are visited in decreasing-degree order (perm) in warp tiles of 32/G rows, so
+//     the groups of a warp have (nearly) the same trip count and stay converged;
 //   * kChunk neighbour rows per group are in flight per trip; the next trip's column
-//     indices and the next tile's row data are prefetched during the current trip;
-//   * L2 policy: rows below the hot bound (the highest-degree rows, sized to a share of
-//     L2) are gathered evict-last, the others evict-first; column indices are loaded
-//     evict-first; outputs of cold rows are stored streaming;
+//     indices and the next tiles' rows (perm entry two tiles ahead, row bounds, self
+//     row, dinv, w one tile ahead) are prefetched during the current trip;
+//   * column indices are loaded evict-first (streamed once); outputs stored streaming;
+//     bf16 neighbour rows are added with mixed-precision adds (one instruction a value);
 //   * wide rows can be split into column chunks (blockIdx.y) over a column-blocked
 //     activation layout so that the gathered slice of T^(l-1) fits L2;
-//   * epilogue per row: self term, tanh, store s_k, and exact integer column sums of t
+//   * epilogue per row: self term, tanh, store s_i, and exact integer column sums of t
 //     and t^2 (fixed point 2^-30); a warp/CTA reduction gives one partial per CTA and
 //     the last CTA to finish (ticket counter) adds them up and forms mean and 1/std
 //     in fp64. Integer sums make the result independent of the row order.
+#include <cuda.h>
+
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -159,16 +156,6 @@ __device__ __forceinline__ int ld_stream(const int* p, uint64_t pol) {
   asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
   return v;
 }
-__device__ __forceinline__ uint64_t evict_normal_policy() {
-  uint64_t pol;
-  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
-  return pol;
-}
-__device__ __forceinline__ uint64_t evict_last_policy() {
-  uint64_t pol;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-  return pol;
-}
 // Rows written by a layer are read again only by the next layer: streaming stores.
 __device__ __forceinline__ void store_chunk_cs(float* p, const float (&v)[4]) {
   __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
@@ -237,17 +224,16 @@ __device__ __forceinline__ void theta8(uint64_t seed, uint64_t i, uint64_t q, fl
 }
 
 // Theta, stored as dinv_i * Theta_i when dinv is given (the layer storage convention).
-// Row i of `out` holds the draw of original node rowid[i] (rowid NULL: node i).
 template <typename S>
 __global__ void k_theta(uint64_t seed, int32_t N, int32_t d, int32_t dc, float xs, const float* __restrict__ dinv,
-                        const int32_t* __restrict__ rowid, S* __restrict__ out) {
+                        S* __restrict__ out) {
   const int nq = d >> 3;
   const int64_t total = (int64_t)N * nq;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t / nq;
     const int q = (int)(t - i * nq);
     float z[8];
-    theta8(seed, (uint64_t)(rowid ? __ldg(rowid + i) : i), (uint64_t)q, xs, z);
+    theta8(seed, (uint64_t)i, (uint64_t)q, xs, z);
     if (dinv) {
       const float di = __ldg(dinv + i);
       if (di > 0.0f) {
@@ -344,58 +330,18 @@ __global__ void k_deg_scatter(const int32_t* __restrict__ row_ptr, int32_t N, in
   }
 }
 
-// inv[perm[k]] = k
-__global__ void k_invert(const int32_t* __restrict__ perm, int32_t N, int32_t* __restrict__ inv) {
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
-    inv[perm[k]] = (int32_t)k;
-}
-// cnt[k] = degree of original row perm[k]; cnt[N] = 0
-__global__ void k_lrow_count(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ perm, int32_t N,
-                             int* __restrict__ cnt) {
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= N; k += (int64_t)gridDim.x * blockDim.x) {
-    if (k == N) {
-      cnt[k] = 0;
-    } else {
-      const int r = perm[k];
-      cnt[k] = row_ptr[r + 1] - row_ptr[r];
-    }
-  }
-}
-// Row k of the relabelled graph: the neighbours of original row perm[k], renamed by inv,
-// in the original (increasing original id) order. One warp per row.
-__global__ void k_relabel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                          const int32_t* __restrict__ perm, const int32_t* __restrict__ inv,
-                          const int32_t* __restrict__ lrow_ptr, int32_t N, int32_t* __restrict__ lcol) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < N;
-       k += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const int r = perm[k];
-    const int b = row_ptr[r], n = row_ptr[r + 1] - b;
-    const int o = lrow_ptr[k];
-    for (int t = lane; t < n; t += 32) lcol[o + t] = inv[col[b + t]];
-  }
-}
-// dst[i] = src[idx[i]]
-__global__ void k_gather_f32(const float* __restrict__ src, const int32_t* __restrict__ idx, int32_t N,
-                             float* __restrict__ dst) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = src[idx[i]];
-}
-
 // A caller-supplied Z^(0) in the storage type, copied into the row-scaled storage.
-// Row i of `out` takes row rowid[i] of x (rowid NULL: row i).
 template <typename S>
-__global__ void k_prescale(const S* __restrict__ x, const float* __restrict__ dinv,
-                           const int32_t* __restrict__ rowid, int32_t N, int32_t d, int32_t dc, S* __restrict__ out) {
+__global__ void k_prescale(const S* __restrict__ x, const float* __restrict__ dinv, int32_t N, int32_t d,
+                           int32_t dc, S* __restrict__ out) {
   constexpr int VPL = Store<S>::VPL;
   const int nc = d / VPL;
   const int64_t total = (int64_t)N * nc;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t / nc;
     const int c = (int)(t - i * nc) * VPL;
-    const int64_t src = rowid ? (int64_t)__ldg(rowid + i) : i;
     float v[VPL];
-    load_chunk(x + src * d + c, v);
+    load_chunk(x + i * d + c, v);
     const float di = __ldg(dinv + i);
     if (di > 0.0f) {
 #pragma unroll
@@ -407,6 +353,12 @@ __global__ void k_prescale(const S* __restrict__ x, const float* __restrict__ di
 
 // ------------------------------------------------------------------ Eq. 4 layer
 constexpr int kChunk = 8;  // neighbour rows in flight per row group per trip
+
+// Build-time tuning of the register-load layer kernel (defaults are the measured best).
+#ifndef IGP_LAYER_MIN_CTAS
+#define IGP_LAYER_MIN_CTAS 2  // resident CTAs per SM the register budget is sized for
+#endif
+
 
 // tanh of Eq. 4. With fp32 storage: CUDA's tanhf. With bf16 storage the result is
 // rounded to 8 significant bits right after, so the hardware approximation (relative
@@ -430,13 +382,6 @@ template <>
 struct Raw<float> {
   using T = float4;
   static __device__ __forceinline__ float4 load(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
-  static __device__ __forceinline__ float4 load_pol(const float* p, uint64_t pol) {
-    float4 v;
-    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p), "l"(pol));
-    return v;
-  }
   static __device__ __forceinline__ float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
   static __device__ __forceinline__ void add(float (&a)[4], float4 x) {
     a[0] += x.x; a[1] += x.y; a[2] += x.z; a[3] += x.w;
@@ -449,13 +394,6 @@ template <>
 struct Raw<__nv_bfloat16> {
   using T = uint4;
   static __device__ __forceinline__ uint4 load(const __nv_bfloat16* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
-  static __device__ __forceinline__ uint4 load_pol(const __nv_bfloat16* p, uint64_t pol) {
-    uint4 v;
-    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p), "l"(pol));
-    return v;
-  }
   static __device__ __forceinline__ uint4 zero() { return make_uint4(0u, 0u, 0u, 0u); }
   // a[2k] += low bf16 of word k, a[2k+1] += high bf16, each one mixed-precision add
   // (bf16 operand, fp32 accumulator and result; the same value as converting first).
@@ -488,16 +426,15 @@ constexpr float kQScale = 1073741824.0f;  // 2^30
 // Chunks are independent (tanh and the column statistics act per column); each has
 // its own partials and ticket.
 //
-// Rows are taken in their own order in warp tiles of GPW consecutive rows, one row per
-// group of G lanes. On the degree-relabelled graph the rows of a tile have (nearly)
-// equal degree, so the groups run their gather loops in lockstep. Rows below `hot` are
-// gathered with an evict-last L2 policy and the others evict-first.
+// Rows are taken in `perm` order (NULL: their own order) in warp tiles of GPW rows, one
+// row per group of G lanes; with perm sorting rows by degree, the rows of a tile have
+// (nearly) equal degree and the groups run their gather loops in lockstep.
 template <int D, typename S>
-__global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
+__global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const float* __restrict__ dinv,
-    const float* __restrict__ wsum, const S* __restrict__ Tin_all, S* __restrict__ Tout_all,
-    const float* __restrict__ stats_in, long long* __restrict__ partials_all, float* __restrict__ stats_out,
-    unsigned* __restrict__ tickets, int32_t N, int32_t d, int32_t hot, int hints, float alpha, float theta,
+    const float* __restrict__ wsum, const int32_t* __restrict__ perm, const S* __restrict__ Tin_all,
+    S* __restrict__ Tout_all, const float* __restrict__ stats_in, long long* __restrict__ partials_all,
+    float* __restrict__ stats_out, unsigned* __restrict__ tickets, int32_t N, int32_t d, float alpha, float theta,
     int ddof) {
   using RW = Raw<S>;
   using RT = typename RW::T;
@@ -526,8 +463,6 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
   }
   __syncthreads();
   const uint64_t pol_first = evict_first_policy();
-  const uint64_t pol_last = hints ? evict_last_policy() : evict_normal_policy();
-  const uint64_t pol_cold = hints ? pol_first : pol_last;
 
   long long qs[VPL], qq[VPL];
 #pragma unroll
@@ -545,17 +480,21 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
       jw[k] = (t < C && base + t < end) ? ld_stream(col + base + t, pol_first) : 0;
     }
   };
+  auto row_at = [&](int64_t tile) -> int {
+    const int64_t p = tile * GPW + grp;
+    if (tile >= ntiles || p >= N) return -1;
+    return perm ? __ldg(perm + p) : (int)p;
+  };
   struct RowData {
     int b, e;
     RT self;
     float di, wi;
   };
-  auto fetch_row = [&](int64_t tile, RowData& rd) {
-    const int64_t r = tile * GPW + grp;
-    if (tile < ntiles && r < N) {
+  auto fetch_row = [&](int r, RowData& rd) {
+    if (r >= 0) {
       rd.b = __ldg(row_ptr + r);
       rd.e = __ldg(row_ptr + r + 1);
-      rd.self = RW::load(Tin + r * D);
+      rd.self = RW::load(Tin + (int64_t)r * D);
       rd.di = __ldg(dinv + r);
       rd.wi = __ldg(wsum + r);
     } else {
@@ -565,15 +504,17 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
     }
   };
 
-  // two-stage pipeline over tiles: row data (t+1) while gathering tile t
+  // three-stage pipeline over tiles: row id (t+2), row data (t+1), gathers (t)
+  int r = row_at(w0);
   RowData cur;
-  fetch_row(w0, cur);
+  fetch_row(r, cur);
+  int r_n = row_at(w0 + nw);
   int jw[IPL];
   load_idx(jw, cur.b, cur.e);
   for (int64_t tile = w0; tile < ntiles; tile += nw) {
-    const int64_t r = tile * GPW + grp;
+    const int r_nn = row_at(tile + 2 * nw);
     RowData nxt;
-    fetch_row(tile + nw, nxt);
+    fetch_row(r_n, nxt);
 
     const int ntrip = (cur.e - cur.b + C - 1) / C;
     const int mtrip = __reduce_max_sync(0xffffffffu, ntrip);
@@ -588,7 +529,7 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
 #pragma unroll
       for (int t = 0; t < C; ++t) {
         const int j = __shfl_sync(0xffffffffu, jw[t / G], t % G, G);
-        x[t] = (c + t < cur.e) ? RW::load_pol(Tin + (int64_t)j * D, j < hot ? pol_last : pol_cold) : RW::zero();
+        x[t] = (c + t < cur.e) ? RW::load(Tin + (int64_t)j * D) : RW::zero();
       }
 #pragma unroll
       for (int t = 0; t < C; ++t) RW::add(acc, x[t]);
@@ -597,7 +538,7 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
     }
     // first trip indices of the next tile, then this tile's epilogue
     load_idx(jw, nxt.b, nxt.e);
-    if (r < N) {
+    if (r >= 0) {
       float sv[VPL];
       RW::unpack(cur.self, sv);
       const bool scaled = cur.di > 0.0f;
@@ -616,11 +557,10 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
         qq[v] += __float2ll_rn(t * t * kQScale);
         o[v] = scaled ? cur.di * t : t;
       }
-      if (r < hot)
-        store_chunk(Tout + r * D, o);
-      else
-        store_chunk_cs(Tout + r * D, o);
+      store_chunk_cs(Tout + (int64_t)r * D, o);
     }
+    r = r_n;
+    r_n = r_nn;
     cur = nxt;
   }
 
@@ -683,11 +623,400 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer(
   if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
 }
 
+// ------------------------------------------------------------------ Eq. 4 layer, bulk-copy gathers
+// The same layer as k_layer, with the neighbour rows brought in by the TMA engine:
+// every warp owns a ring of kTmaStages shared-memory stages (one trip each: 32/G rows x
+// kChunk neighbours = 4 KB) completed by mbarriers. Each neighbour row is one
+// cp.async.bulk copy issued by the lane that holds its column index, so no registers
+// are tied up while rows are in flight and the warp keeps kTmaStages trips in flight;
+// lanes then add the rows from shared memory. Waits are bounded (about a second); a
+// warp that gives up sets *err, waits (bounded) for its own copies and returns.
+constexpr int kTmaStages = 3;
+constexpr int kTmaStageBytes = 32 * kChunk * 16;  // rows per trip x row bytes, for any width
+constexpr unsigned long long kWaitNs = 1000000000ull;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of an mbarrier; false if it did not complete in time.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  if (mbar_try_wait(mbar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    for (int k = 0; k < 64; ++k)
+      if (mbar_try_wait(mbar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+template <typename S>
+struct RawSm;
+template <>
+struct RawSm<float> {
+  static __device__ __forceinline__ void add(float (&a)[4], uint32_t addr) {
+    float4 x;
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w) : "r"(addr));
+    a[0] += x.x; a[1] += x.y; a[2] += x.z; a[3] += x.w;
+  }
+};
+template <>
+struct RawSm<__nv_bfloat16> {
+  static __device__ __forceinline__ void add(float (&a)[8], uint32_t addr) {
+    uint4 x;
+    asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(x.x), "=r"(x.y), "=r"(x.z), "=r"(x.w) : "r"(addr));
+    Raw<__nv_bfloat16>::add(a, x);
+  }
+};
+
+// MODE 1: one cp.async.bulk copy per neighbour row, issued by the lane holding its index.
+// MODE 4: cp.async.bulk.tensor tile::gather4 through a tensor map of T^(l-1) (box one row
+//         high), four neighbour rows per copy; needs a single column block.
+template <int D, typename S, int MODE>
+__global__ void __launch_bounds__(kLayerThreads, 2) k_layer_tma(
+    const __grid_constant__ CUtensorMap tmap, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+    const float* __restrict__ dinv, const float* __restrict__ wsum, const int32_t* __restrict__ perm,
+    const S* __restrict__ Tin_all,
+    S* __restrict__ Tout_all, const float* __restrict__ stats_in, long long* __restrict__ partials_all,
+    float* __restrict__ stats_out, unsigned* __restrict__ tickets, int* __restrict__ err, int32_t N, int32_t d,
+    float alpha, float theta, int ddof, int withhold) {
+  using RW = Raw<S>;
+  using RT = typename RW::T;
+  constexpr int VPL = Store<S>::VPL;
+  constexpr int G = D / VPL;               // lanes per row
+  constexpr int GPW = 32 / G;              // rows per warp tile
+  constexpr int C = kChunk;                // neighbour rows per row per trip
+  constexpr int IPL = C >= G ? C / G : 1;  // trip entries held per lane
+  constexpr int RB = D * (int)sizeof(S);   // bytes per row
+  static_assert(GPW * C * RB == kTmaStageBytes, "stage size");
+  static_assert(RB % 16 == 0, "bulk copies need 16-byte rows");
+
+  extern __shared__ __align__(128) unsigned char dyn[];
+  __shared__ float s_mu[D], s_is[D];
+  __shared__ long long s_red[kLayerWarps][2 * D];
+  __shared__ bool s_last;
+  __shared__ int s_fail;
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / G, lig = lane % G;
+  const int c0 = blockIdx.y * D;
+  const int64_t blk = (int64_t)blockIdx.y * N * D;
+  if (threadIdx.x == 0) s_fail = 0;
+  const S* __restrict__ Tin = Tin_all + blk;  // row r of this column block at Tin + r * D
+  S* __restrict__ Tout = Tout_all + blk + lig * VPL;
+  long long* __restrict__ partials = partials_all + (int64_t)blockIdx.y * gridDim.x * 2 * D;
+  unsigned* ticket = tickets + blockIdx.y;
+  const uint32_t ring = smem_addr(dyn) + warp * kTmaStages * kTmaStageBytes;
+  const uint32_t mbar0 = smem_addr(dyn) + kLayerWarps * kTmaStages * kTmaStageBytes + warp * kTmaStages * 8;
+  for (int c = threadIdx.x; c < D; c += blockDim.x) {
+    s_mu[c] = stats_in ? stats_in[c0 + c] : 0.0f;
+    s_is[c] = stats_in ? stats_in[d + c0 + c] : 1.0f;
+  }
+  if (lane == 0) {
+    for (int k = 0; k < kTmaStages; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0 + 8 * k));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const uint64_t pol_first = evict_first_policy();
+
+  long long qs[VPL], qq[VPL];
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) qs[v] = qq[v] = 0;
+
+  const int64_t ntiles = ((int64_t)N + GPW - 1) / GPW;
+  const int64_t nw = (int64_t)gridDim.x * kLayerWarps;
+  const int64_t w0 = (int64_t)blockIdx.x * kLayerWarps + warp;
+
+  auto load_idx = [&](int (&jw)[IPL], int base, int end) {
+#pragma unroll
+    for (int k = 0; k < IPL; ++k) {
+      const int t = lig + G * k;
+      jw[k] = (t < C && base + t < end) ? ld_stream(col + base + t, pol_first) : 0;
+    }
+  };
+  auto row_at = [&](int64_t tile) -> int {
+    const int64_t p = tile * GPW + grp;
+    if (tile >= ntiles || p >= N) return -1;
+    return perm ? __ldg(perm + p) : (int)p;
+  };
+  auto bounds = [&](int64_t tile, int& b, int& e) {
+    const int r = row_at(tile);
+    if (r >= 0) {
+      b = __ldg(row_ptr + r);
+      e = __ldg(row_ptr + r + 1);
+    } else {
+      b = e = 0;
+    }
+  };
+  auto trips = [&](int b, int e) { return __reduce_max_sync(0xffffffffu, (e - b + C - 1) / C); };
+
+  // ---- producer: walks the same tiles and trips as the consumer, up to kTmaStages ahead
+  int64_t p_tile = w0;
+  int p_trip = 0, p_b, p_e, p_nb, p_ne;
+  bounds(p_tile, p_b, p_e);
+  bounds(p_tile + nw, p_nb, p_ne);
+  int p_mtrip = trips(p_b, p_e);
+  int p_jw[IPL];
+  load_idx(p_jw, p_b, p_e);
+  uint32_t issued = 0;
+  // move the producer to the next tile that has trips (or past the end)
+  auto p_next_tile = [&]() {
+    for (;;) {
+      p_tile += nw;
+      p_trip = 0;
+      p_b = p_nb;
+      p_e = p_ne;
+      bounds(p_tile + nw, p_nb, p_ne);
+      if (p_tile >= ntiles) return;
+      p_mtrip = trips(p_b, p_e);
+      if (p_mtrip > 0) return;
+    }
+  };
+  if (p_mtrip == 0 && p_tile < ntiles) {
+    p_next_tile();
+    load_idx(p_jw, p_b, p_e);
+  }
+  auto issue = [&]() {
+    const uint32_t stage = issued % kTmaStages;
+    const uint32_t mbar = mbar0 + 8 * stage;
+    const int base = p_b + p_trip * C;
+    // (withhold != 0 only in the test of the bounded wait: the first trip of the first warp
+    // announces its bytes but issues no copy, so that wait runs out)
+    const bool skip = withhold && issued == 0 && blockIdx.x == 0 && blockIdx.y == 0 && warp == 0;
+    if constexpr (MODE == 1) {
+      int cnt = 0;
+#pragma unroll
+      for (int k = 0; k < IPL; ++k) {
+        const int t = lig + G * k;
+        cnt += __popc(__ballot_sync(0xffffffffu, t < C && base + t < p_e));
+      }
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(cnt * RB) : "memory");
+      __syncwarp();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+#pragma unroll
+      for (int k = 0; k < IPL; ++k) {
+        const int t = lig + G * k;
+        if (t < C && base + t < p_e && !skip) {
+          const uint32_t dst = ring + stage * kTmaStageBytes + (grp * C + t) * RB;
+          asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                       "l"(Tin + (int64_t)p_jw[k] * D), "r"(RB), "r"(mbar)
+                       : "memory");
+        }
+      }
+    } else {
+      // lane q < NOPS issues gather4 #q: stage slots 4q..4q+3 = entries t0..t0+3 of group g
+      constexpr int NOPS = GPW * C / 4;
+      const int q = lane;
+      const int g = (4 * q) / C, t0 = (4 * q) % C;
+      const int gl = (g * G) & 31;  // a lane of group g
+      const int gbase = __shfl_sync(0xffffffffu, base, gl);
+      const int gend = __shfl_sync(0xffffffffu, p_e, gl);
+      int rows[4];
+      bool any = false;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int t = t0 + u;
+        const int src = (g * G + (t % G)) & 31;
+        int v = 0;
+#pragma unroll
+        for (int k = 0; k < IPL; ++k) {
+          const int w = __shfl_sync(0xffffffffu, p_jw[k], src);
+          if (k == t / G) v = w;
+        }
+        const bool valid = q < NOPS && gbase + t < gend;
+        rows[u] = valid ? v : 0;  // unused slots read row 0 and are not added
+        any |= valid;
+      }
+      const int ops = __popc(__ballot_sync(0xffffffffu, any));
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(ops * 4 * RB)
+                     : "memory");
+      __syncwarp();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (any && !skip) {
+        const uint32_t dst = ring + stage * kTmaStageBytes + 4 * q * RB;
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+            "%3, %4, %5, %6}], [%7];" ::"r"(dst),
+            "l"(&tmap), "r"(0), "r"(rows[0]), "r"(rows[1]), "r"(rows[2]), "r"(rows[3]), "r"(mbar)
+            : "memory");
+      }
+    }
+    ++issued;
+    if (++p_trip == p_mtrip) p_next_tile();
+    if (p_tile < ntiles) load_idx(p_jw, p_b + p_trip * C, p_e);
+  };
+  while (p_tile < ntiles && issued < (uint32_t)kTmaStages) issue();
+
+  // ---- consumer
+  struct RowData {
+    int b, e;
+    RT self;
+    float di, wi;
+  };
+  auto fetch_row = [&](int r, RowData& rd) {
+    if (r >= 0) {
+      rd.b = __ldg(row_ptr + r);
+      rd.e = __ldg(row_ptr + r + 1);
+      rd.self = RW::load(Tin + (int64_t)r * D + lig * VPL);
+      rd.di = __ldg(dinv + r);
+      rd.wi = __ldg(wsum + r);
+    } else {
+      rd.b = rd.e = 0;
+      rd.self = RW::zero();
+      rd.di = rd.wi = 0.0f;
+    }
+  };
+  uint32_t consumed = 0;
+  bool failed = false;
+  int r = row_at(w0);
+  RowData cur;
+  fetch_row(r, cur);
+  int r_n = row_at(w0 + nw);
+  for (int64_t tile = w0; tile < ntiles; tile += nw) {
+    const int r_nn = row_at(tile + 2 * nw);
+    RowData nxt;
+    fetch_row(r_n, nxt);
+    const int mtrip = trips(cur.b, cur.e);
+    float acc[VPL];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) acc[v] = 0.0f;
+    for (int tr = 0; tr < mtrip; ++tr) {
+      const uint32_t stage = consumed % kTmaStages;
+      const uint32_t parity = (consumed / kTmaStages) & 1u;
+      if (!__all_sync(0xffffffffu, mbar_wait(mbar0 + 8 * stage, parity))) {  // warp-uniform
+        failed = true;
+        break;
+      }
+      const int c = cur.b + tr * C;
+      const uint32_t src = ring + stage * kTmaStageBytes + grp * C * RB + lig * 16;
+#pragma unroll
+      for (int t = 0; t < C; ++t)
+        if (c + t < cur.e) RawSm<S>::add(acc, src + t * RB);
+      __syncwarp();
+      ++consumed;
+      if (p_tile < ntiles) issue();
+    }
+    if (__any_sync(0xffffffffu, failed)) {
+      failed = true;
+      break;
+    }
+    if (r >= 0) {
+      float sv[VPL];
+      RW::unpack(cur.self, sv);
+      const bool scaled = cur.di > 0.0f;
+      const float rdi = scaled ? __frcp_rn(cur.di) : 1.0f;
+      float o[VPL];
+#pragma unroll
+      for (int v = 0; v < VPL; ++v) {
+        const int cidx = lig * VPL + v;
+        const float mu = s_mu[cidx], is = s_is[cidx];
+        const float ti = scaled ? sv[v] * rdi : sv[v];
+        const float zi = (ti - mu) * is;
+        const float agg = is * fmaf(-mu, cur.wi, acc[v]);
+        const float y = fmaf(theta, zi, alpha * cur.di * agg);
+        const float t = tanh_for<S>(y);
+        qs[v] += __float2ll_rn(t * kQScale);
+        qq[v] += __float2ll_rn(t * t * kQScale);
+        o[v] = scaled ? cur.di * t : t;
+      }
+      store_chunk_cs(Tout + (int64_t)r * D, o);
+    }
+    r = r_n;
+    r_n = r_nn;
+    cur = nxt;
+  }
+  if (failed) {
+    // record, and wait (bounded) for this warp's copies still in flight; the CTA then
+    // skips its ticket, so this layer's statistics are not formed
+    if (lane == 0) {
+      atomicOr(err, 1);
+      s_fail = 1;
+    }
+    while (consumed < issued) {
+      const uint32_t stage = consumed % kTmaStages;
+      (void)mbar_wait(mbar0 + 8 * stage, (consumed / kTmaStages) & 1u);
+      ++consumed;
+    }
+  }
+
+  // ---- column statistics: exact integer sums over groups, warps, CTAs
+#pragma unroll
+  for (int m = G; m < 32; m <<= 1) {
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+      qs[v] += __shfl_xor_sync(0xffffffffu, qs[v], m);
+      qq[v] += __shfl_xor_sync(0xffffffffu, qq[v], m);
+    }
+  }
+  if (grp == 0) {
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+      s_red[warp][lig * VPL + v] = qs[v];
+      s_red[warp][D + lig * VPL + v] = qq[v];
+    }
+  }
+  __syncthreads();
+  if (s_fail) return;  // uniform over the CTA
+  for (int c = threadIdx.x; c < 2 * D; c += blockDim.x) {
+    long long a = 0;
+#pragma unroll
+    for (int w = 0; w < kLayerWarps; ++w) a += s_red[w][c];
+    partials[(int64_t)blockIdx.x * 2 * D + c] = a;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  constexpr int R0 = kLayerThreads / (2 * D) > 0 ? kLayerThreads / (2 * D) : 1;
+  constexpr int R = R0 < kLayerWarps ? R0 : kLayerWarps;
+  long long* s_tot = &s_red[0][0];  // reuse: R * 2D <= kLayerWarps * 2D
+  for (int t = threadIdx.x; t < R * 2 * D; t += blockDim.x) {
+    const int c = t % (2 * D), rr = t / (2 * D);
+    long long a = 0;
+    for (int b = rr; b < (int)gridDim.x; b += R) a += __ldcg(partials + (int64_t)b * 2 * D + c);
+    s_tot[rr * 2 * D + c] = a;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < D; c += blockDim.x) {
+    long long sa = 0, qa = 0;
+    for (int rr = 0; rr < R; ++rr) {
+      sa += s_tot[rr * 2 * D + c];
+      qa += s_tot[rr * 2 * D + D + c];
+    }
+    const double n = (double)N;
+    const double st = (double)sa * (1.0 / (double)(1ll << kQBits));  // sum of t
+    const double sq = (double)qa * (1.0 / (double)(1ll << kQBits));  // sum of t^2
+    const double mean = st / n;
+    const double denom = n - (double)ddof;
+    double var = denom > 0.0 ? (sq - st * mean) / denom : 0.0;
+    if (!(var > 0.0)) var = 0.0;
+    const double sd = sqrt(var);
+    stats_out[c0 + c] = (float)mean;
+    stats_out[d + c0 + c] = sd > 0.0 ? (float)(1.0 / sd) : 0.0f;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
+}
+
+
 // ------------------------------------------------------------------ output
 template <int D, typename S>
 __global__ void k_output(const S* __restrict__ T, const float* __restrict__ dinv, const float* __restrict__ stats,
-                         const int32_t* __restrict__ rowid, int32_t N, int32_t dc, int row_l2,
-                         float* __restrict__ out) {
+                         int32_t N, int32_t dc, int row_l2, float* __restrict__ out) {
   constexpr int VPL = Store<S>::VPL;
   constexpr int G = D / VPL;  // lanes per row
   constexpr int RPW = 32 / G;  // rows per warp pass
@@ -726,7 +1055,7 @@ __global__ void k_output(const S* __restrict__ T, const float* __restrict__ dinv
       for (int e = 0; e < VPL; ++e) o[e] *= inv;
     }
     if (ok) {
-      float* p = out + (rowid ? (int64_t)__ldg(rowid + i) : i) * D + chunk * VPL;  // original row
+      float* p = out + i * D + chunk * VPL;
 #pragma unroll
       for (int e = 0; e < VPL; e += 4)
         *reinterpret_cast<float4*>(p + e) = make_float4(o[e], o[e + 1], o[e + 2], o[e + 3]);
@@ -759,48 +1088,139 @@ struct LayerCfg {
 template <int D, typename S>
 igp_status layer_launch(const LayerArgs& a, cudaStream_t s) {
   dim3 gr(a.grid, a.d / D);
-  k_layer<D, S><<<gr, kLayerThreads, 0, s>>>(a.row_ptr, a.col, a.dinv, a.wsum, (const S*)a.Tin, (S*)a.Tout,
-                                             a.stats_in, a.partials, a.stats_out, a.tickets, a.N, a.d, a.hot,
-                                             a.hints, a.alpha, a.theta, a.ddof);
+  k_layer<D, S><<<gr, kLayerThreads, 0, s>>>(a.row_ptr, a.col, a.dinv, a.wsum, a.perm, (const S*)a.Tin,
+                                             (S*)a.Tout, a.stats_in, a.partials, a.stats_out, a.tickets, a.N, a.d,
+                                             a.alpha, a.theta, a.ddof);
   return after_launch("k_layer");
 }
 
+constexpr size_t kTmaDynSmem = (size_t)kLayerWarps * kTmaStages * (kTmaStageBytes + 8);
+
 template <int D, typename S>
-igp_status output_launch(const void* T, const float* dinv, const float* st, const int32_t* rowid, int32_t N, int dc,
-                         int row_l2, float* out, cudaStream_t s) {
+struct TmaCfg {
+  static int per_sm() {
+    static int v = 0;
+    if (v == 0) {
+      cudaFuncSetAttribute(k_layer_tma<D, S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaDynSmem);
+      int b = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_layer_tma<D, S, 1>, kLayerThreads, kTmaDynSmem);
+      v = b > 0 ? b : 1;
+    }
+    return v;
+  }
+  static constexpr int GPW = 32 / (D / Store<S>::VPL);
+  static int grid(int32_t N) {
+    const int64_t rows_per_cta = (int64_t)kLayerWarps * GPW;
+    const int64_t want = ((int64_t)N + rows_per_cta - 1) / rows_per_cta;
+    const int64_t cap = (int64_t)per_sm() * num_sms();
+    return (int)std::max<int64_t>(1, std::min(want, cap));
+  }
+};
+
+// cuTensorMapEncodeTiled, looked up once from the driver (no link-time dependency).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+igp_status encode_tiled_fn(EncodeTiledFn* fn) {
+  static EncodeTiledFn f = nullptr;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!f) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) {
+      set_error("cuTensorMapEncodeTiled is not available from the driver");
+      return IGP_E_UNSUPPORTED;
+    }
+    f = (EncodeTiledFn)p;
+  }
+  *fn = f;
+  return IGP_OK;
+}
+
+// Tensor map of an N x D activation block (rows of D values), boxes one row high.
+template <int D, typename S>
+igp_status make_row_map(const void* base, int32_t N, CUtensorMap* m) {
+  EncodeTiledFn fn;
+  IGP_TRY(encode_tiled_fn(&fn));
+  const cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)N};
+  const cuuint64_t strides[1] = {(cuuint64_t)D * sizeof(S)};
+  const cuuint32_t box[2] = {(cuuint32_t)D, 1u};
+  const cuuint32_t estr[2] = {1u, 1u};
+  const CUtensorMapDataType dt = sizeof(S) == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  CUresult r = fn(m, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) for a %d x %d map", (int)r, N, D);
+    return IGP_E_CUDA;
+  }
+  return IGP_OK;
+}
+
+template <int D, typename S>
+igp_status layer_tma_launch(const LayerArgs& a, cudaStream_t s) {
+  dim3 gr(a.grid, a.d / D);
+  CUtensorMap m;
+  memset(&m, 0, sizeof(m));
+  if (a.gather4) {
+    if (a.d != D) {
+      set_error("gather4 needs a single column block");
+      return IGP_E_INVAL;
+    }
+    const igp_status ms = make_row_map<D, S>(a.Tin, a.N, &m);
+    if (ms != IGP_OK) return ms;
+    IGP_TRY_CUDA(
+        cudaFuncSetAttribute(k_layer_tma<D, S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaDynSmem));
+    k_layer_tma<D, S, 4><<<gr, kLayerThreads, kTmaDynSmem, s>>>(
+        m, a.row_ptr, a.col, a.dinv, a.wsum, a.perm, (const S*)a.Tin, (S*)a.Tout, a.stats_in, a.partials, a.stats_out,
+        a.tickets, a.err, a.N, a.d, a.alpha, a.theta, a.ddof, a.withhold);
+  } else {
+    IGP_TRY_CUDA(
+        cudaFuncSetAttribute(k_layer_tma<D, S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaDynSmem));
+    k_layer_tma<D, S, 1><<<gr, kLayerThreads, kTmaDynSmem, s>>>(
+        m, a.row_ptr, a.col, a.dinv, a.wsum, a.perm, (const S*)a.Tin, (S*)a.Tout, a.stats_in, a.partials, a.stats_out,
+        a.tickets, a.err, a.N, a.d, a.alpha, a.theta, a.ddof, a.withhold);
+  }
+  return after_launch("k_layer_tma");
+}
+
+template <int D, typename S>
+igp_status output_launch(const void* T, const float* dinv, const float* st, int32_t N, int dc, int row_l2, float* out,
+                         cudaStream_t s) {
   constexpr int G = D / Store<S>::VPL;
   int64_t threads = (int64_t)N * G;
   int blocks = (int)std::min<int64_t>((threads + 255) / 256, (int64_t)num_sms() * 16);
-  k_output<D, S><<<std::max(blocks, 1), 256, 0, s>>>((const S*)T, dinv, st, rowid, N, dc, row_l2, out);
+  k_output<D, S><<<std::max(blocks, 1), 256, 0, s>>>((const S*)T, dinv, st, N, dc, row_l2, out);
   return after_launch("k_output");
 }
 
 template <typename S>
-igp_status prescale_launch(const void* x, const float* dinv, const int32_t* rowid, int32_t N, int32_t d, int32_t dc,
-                           void* out, cudaStream_t s) {
+igp_status prescale_launch(const void* x, const float* dinv, int32_t N, int32_t d, int32_t dc, void* out,
+                           cudaStream_t s) {
   int64_t total = (int64_t)N * d / Store<S>::VPL;
   int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms() * 16);
-  k_prescale<S><<<std::max(blocks, 1), 256, 0, s>>>((const S*)x, dinv, rowid, N, d, dc, (S*)out);
+  k_prescale<S><<<std::max(blocks, 1), 256, 0, s>>>((const S*)x, dinv, N, d, dc, (S*)out);
   return after_launch("k_prescale");
 }
 
 struct Ops {
   int (*grid)(int32_t);
   igp_status (*layer)(const LayerArgs&, cudaStream_t);
-  igp_status (*output)(const void*, const float*, const float*, const int32_t*, int32_t, int, int, float*,
-                       cudaStream_t);
-  igp_status (*prescale)(const void*, const float*, const int32_t*, int32_t, int32_t, int32_t, void*, cudaStream_t);
+  int (*tma_grid)(int32_t);
+  igp_status (*layer_tma)(const LayerArgs&, cudaStream_t);
+  igp_status (*output)(const void*, const float*, const float*, int32_t, int, int, float*, cudaStream_t);
+  igp_status (*prescale)(const void*, const float*, int32_t, int32_t, int32_t, void*, cudaStream_t);
 };
 
 template <int D, typename S>
 Ops ops_for() {
-  return Ops{&LayerCfg<D, S>::grid, &layer_launch<D, S>, &output_launch<D, S>, &prescale_launch<S>};
+  return Ops{&LayerCfg<D, S>::grid, &layer_launch<D, S>, &TmaCfg<D, S>::grid, &layer_tma_launch<D, S>,
+             &output_launch<D, S>, &prescale_launch<S>};
 }
 
 // L2 budget for the gathered chunk of T^(l-1): chunks of at most this many bytes.
 constexpr size_t kChunkBytes = 72ull << 20;
-// Share of L2 given to the most-gathered rows (evict-last); the rest is for streams.
-constexpr size_t kHotBytes = 48ull << 20;
 
 // Column chunk width for a layer: the widest of d, d/2, d/4, .. whose N x width slice
 // fits the L2 budget, but never below 128 bytes per row: a gathered row segment is then
@@ -812,12 +1232,13 @@ int chunk_width(int32_t N, int d, size_t sb) {
   return w;
 }
 
-// Number of leading (highest-degree) rows gathered with the evict-last policy
-// (hot_bytes 0: the default share; negative: no L2 priority hints at all).
-int32_t hot_rows(int32_t N, int dc, size_t sb, int64_t hot_bytes) {
-  if (hot_bytes < 0) return 0;
-  const int64_t hb = hot_bytes > 0 ? hot_bytes : (int64_t)kHotBytes;
-  return (int32_t)std::min<int64_t>(N, hb / ((int64_t)dc * (int64_t)sb));
+// Gather mechanism of a layer: register loads unless a TMA mode is asked for (measured:
+// for 128-byte rows at 2M nodes, per-row bulk copies and gather4 copies were 1.8x and
+// 1.3x slower than register loads).
+bool use_tma(int gather, int dc, size_t sb) {
+  if (gather == IGP_GATHER_LSU) return false;
+  if (gather == IGP_GATHER_BULK || gather == IGP_GATHER_TMA4) return dc * sb >= 16;
+  return false;
 }
 
 bool get_ops(int d, int storage, Ops* o) {
@@ -844,85 +1265,50 @@ igp_status launch_dinv_wsum(const int32_t* row_ptr, const int32_t* col, int32_t 
 
 }  // namespace
 
-// Rows by decreasing degree (g->perm), its inverse and the relabelled CSR, once per graph.
-igp_status ensure_layer_csr(igp_graph* g, cudaStream_t s) {
-  if (g->lcol) return IGP_OK;
+// Rows by decreasing degree (g->perm), once per graph.
+igp_status ensure_perm(igp_graph* g, cudaStream_t s) {
+  if (g->perm) return IGP_OK;
   const int32_t N = g->N;
   const int64_t nb = (int64_t)g->max_deg + 1;
-  const int64_t n1 = (int64_t)N + 1;
-  // owned block: perm[N] | inv[N] | lrow_ptr[N+1]; lcol separately
   void* p = nullptr;
-  IGP_TRY(dev_alloc(&p, (size_t)(3 * (int64_t)N + 1) * sizeof(int32_t), s));
+  IGP_TRY(dev_alloc(&p, (size_t)N * sizeof(int32_t), s));
   int32_t* perm = (int32_t*)p;
-  int32_t* inv = perm + N;
-  int32_t* lrow_ptr = inv + N;
-  void* lc = nullptr;
-  igp_status st = dev_alloc(&lc, (size_t)std::max<int64_t>(g->nnz, 1) * sizeof(int32_t), s);
-  if (st != IGP_OK) {
-    dev_free(p, s);
-    return st;
-  }
-  int32_t* lcol = (int32_t*)lc;
-  // temporaries: hist | off | cur (nb + 1 each) | cnt (N + 1) | scan tiles
-  const int64_t m = std::max<int64_t>(nb + 1, n1);
-  const int64_t ntiles = (m + 8191) / 8192;
   void* t = nullptr;
-  st = dev_alloc(&t, (size_t)(3 * (nb + 1) + n1 + ntiles) * sizeof(int), s);
+  const int64_t ntiles = (nb + 1 + 8191) / 8192;
+  igp_status st = dev_alloc(&t, (size_t)(3 * (nb + 1) + ntiles) * sizeof(int), s);
   if (st != IGP_OK) {
-    dev_free(lc, s);
     dev_free(p, s);
     return st;
   }
   int* hist = (int*)t;
   int* off = hist + (nb + 1);
   int* cur = off + (nb + 1);
-  int* cnt = cur + (nb + 1);
-  int* tmp = cnt + n1;
+  int* tmp = cur + (nb + 1);
   if (cudaMemsetAsync(hist, 0, (nb + 1) * sizeof(int), s) != cudaSuccess ||
       cudaMemsetAsync(cur, 0, (nb + 1) * sizeof(int), s) != cudaSuccess)
     st = cuda_status(cudaGetLastError(), "memset", __FILE__, __LINE__);
-  const int pblocks = (int)(((int64_t)N + kPermRowsPerBlock - 1) / kPermRowsPerBlock);
+  const int blocks = (int)(((int64_t)N + kPermRowsPerBlock - 1) / kPermRowsPerBlock);
   const size_t smem = nb <= kPermSmemBins ? (size_t)nb * sizeof(int) : 0;
-  const int blocks = (int)std::min<int64_t>((n1 + 255) / 256, (int64_t)num_sms() * 8);
-  const int wblocks = (int)std::min<int64_t>(((int64_t)N * 32 + 255) / 256, (int64_t)num_sms() * 16);
   if (st == IGP_OK) {
-    k_deg_hist<<<pblocks, 512, smem, s>>>(g->row_ptr, N, g->max_deg, hist);
+    k_deg_hist<<<blocks, 512, smem, s>>>(g->row_ptr, N, g->max_deg, hist);
     st = after_launch("k_deg_hist");
   }
   if (st == IGP_OK) st = exclusive_scan(hist, off, nb + 1, tmp, s);
   if (st == IGP_OK) {
-    k_deg_scatter<<<pblocks, 512, smem, s>>>(g->row_ptr, N, g->max_deg, off, cur, perm);
+    k_deg_scatter<<<blocks, 512, smem, s>>>(g->row_ptr, N, g->max_deg, off, cur, perm);
     st = after_launch("k_deg_scatter");
-  }
-  if (st == IGP_OK) {
-    k_invert<<<std::max(blocks, 1), 256, 0, s>>>(perm, N, inv);
-    st = after_launch("k_invert");
-  }
-  if (st == IGP_OK) {
-    k_lrow_count<<<std::max(blocks, 1), 256, 0, s>>>(g->row_ptr, perm, N, cnt);
-    st = after_launch("k_lrow_count");
-  }
-  if (st == IGP_OK) st = exclusive_scan(cnt, lrow_ptr, n1, tmp, s);
-  if (st == IGP_OK) {
-    k_relabel<<<std::max(wblocks, 1), 256, 0, s>>>(g->row_ptr, g->col, perm, inv, lrow_ptr, N, lcol);
-    st = after_launch("k_relabel");
   }
   dev_free(t, s);
   if (st != IGP_OK) {
-    dev_free(lc, s);
     dev_free(p, s);
     return st;
   }
   g->perm = perm;
-  g->inv = inv;
-  g->lrow_ptr = lrow_ptr;
-  g->lcol = lcol;
   return IGP_OK;
 }
 
 igp_status compute_dinv(igp_graph* g, double tau, double eps, cudaStream_t s, Profile* prof) {
   if (g->dinv_valid && g->dinv_tau == tau && g->dinv_eps == eps) return IGP_OK;
-  IGP_TRY(ensure_layer_csr(g, s));
   if (!g->dinv) {
     void* p = nullptr;
     IGP_TRY(dev_alloc(&p, (size_t)g->N * 2 * sizeof(float), s));
@@ -930,28 +1316,22 @@ igp_status compute_dinv(igp_graph* g, double tau, double eps, cudaStream_t s, Pr
     g->wsum = g->dinv + g->N;
   }
   PhaseTimer pt(prof, IGP_PHASE_DINV, s);
-  IGP_TRY(launch_dinv_wsum(g->lrow_ptr, g->lcol, g->N, tau, eps, g->dinv, g->wsum, s));
+  IGP_TRY(launch_dinv_wsum(g->row_ptr, g->col, g->N, tau, eps, g->dinv, g->wsum, s));
   g->dinv_valid = true;
   g->dinv_tau = tau;
   g->dinv_eps = eps;
   return IGP_OK;
 }
 
-igp_status dinv_original_order(igp_graph* g, float* out, cudaStream_t s) {
-  int blocks = (int)std::min<int64_t>(((int64_t)g->N + 255) / 256, (int64_t)num_sms() * 8);
-  k_gather_f32<<<std::max(blocks, 1), 256, 0, s>>>(g->dinv, g->inv, g->N, out);
-  return after_launch("k_gather_f32");
-}
-
 igp_status launch_theta(uint64_t seed, int32_t N, int32_t d, int32_t dc, float xs, int storage, const float* dinv,
-                        const int32_t* rowid, void* out, cudaStream_t s) {
+                        void* out, cudaStream_t s) {
   int64_t total = (int64_t)N * (d / 8);
   int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms() * 16);
   blocks = std::max(blocks, 1);
   if (storage == IGP_STORE_BF16)
-    k_theta<__nv_bfloat16><<<blocks, 256, 0, s>>>(seed, N, d, dc, xs, dinv, rowid, (__nv_bfloat16*)out);
+    k_theta<__nv_bfloat16><<<blocks, 256, 0, s>>>(seed, N, d, dc, xs, dinv, (__nv_bfloat16*)out);
   else
-    k_theta<float><<<blocks, 256, 0, s>>>(seed, N, d, dc, xs, dinv, rowid, (float*)out);
+    k_theta<float><<<blocks, 256, 0, s>>>(seed, N, d, dc, xs, dinv, (float*)out);
   return after_launch("k_theta");
 }
 
@@ -967,14 +1347,20 @@ igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed
     return IGP_E_INVAL;
   }
   const int nchunks = d / dc;
-  IGP_TRY(compute_dinv(g, tau, o.eps, s, prof));  // also builds the relabelled CSR
-  const int grid = lops.grid(N);
-  // workspace: T0 | T1 | stats[2][2d] | partials[nchunks][grid][2dc] | tickets[nchunks]
+  IGP_TRY(compute_dinv(g, tau, o.eps, s, prof));
+  IGP_TRY(ensure_perm(g, s));
+  const bool tma = use_tma(o.gather, dc, sb);
+  if (o.gather == IGP_GATHER_TMA4 && dc != d) {
+    set_error("igp_embed: gather4 needs the whole row in one pass (chunk_cols = 0 or d)");
+    return IGP_E_INVAL;
+  }
+  const int grid = tma ? lops.tma_grid(N) : lops.grid(N);
+  // workspace: T0 | T1 | stats[2][2d] | partials[nchunks][grid][2dc] | err, tickets[nchunks]
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t bT = al((size_t)N * d * sb);
   const size_t bS = al(2 * 2 * (size_t)d * sizeof(float));
   const size_t bP = al((size_t)nchunks * grid * 2 * dc * sizeof(long long));
-  const size_t bK = al((size_t)nchunks * sizeof(unsigned));
+  const size_t bK = al((size_t)(nchunks + 1) * sizeof(unsigned));
   const size_t need = 2 * bT + bS + bP + bK;
   if (g->ws_bytes < need) {
     if (g->ws) dev_free(g->ws, s);
@@ -990,29 +1376,33 @@ igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed
   void* T1 = base + bT;
   float* stats = (float*)(base + 2 * bT);
   long long* partials = (long long*)(base + 2 * bT + bS);
-  unsigned* tickets = (unsigned*)(base + 2 * bT + bS + bP);
-  IGP_TRY_CUDA(cudaMemsetAsync(tickets, 0, nchunks * sizeof(unsigned), s));
+  int* err = (int*)(base + 2 * bT + bS + bP);
+  unsigned* tickets = (unsigned*)(err + 1);
+  IGP_TRY_CUDA(cudaMemsetAsync(err, 0, (nchunks + 1) * sizeof(unsigned), s));
 
   {
     PhaseTimer pt(prof, IGP_PHASE_THETA, s);
     if (o.x_in) {
-      IGP_TRY(ops.prescale(o.x_in, g->dinv, g->perm, N, d, dc, T0, s));
+      IGP_TRY(ops.prescale(o.x_in, g->dinv, N, d, dc, T0, s));
     } else {
       const double xs = o.x_scale > 0 ? o.x_scale : 1.0 / std::sqrt((double)d);
-      IGP_TRY(launch_theta(seed, N, d, dc, (float)xs, o.storage, g->dinv, g->perm, T0, s));
+      IGP_TRY(launch_theta(seed, N, d, dc, (float)xs, o.storage, g->dinv, T0, s));
     }
   }
   LayerArgs la;
-  la.row_ptr = g->lrow_ptr;
-  la.col = g->lcol;
+  la.row_ptr = g->row_ptr;
+  la.col = g->col;
+  la.perm = g->perm;
   la.dinv = g->dinv;
   la.wsum = g->wsum;
   la.partials = partials;
   la.tickets = tickets;
+  la.err = err;
+  la.withhold = o.reserved_test;
+  la.gather4 = o.gather == IGP_GATHER_TMA4;
   la.N = N;
   la.d = d;
-  la.hot = hot_rows(N, dc, sb, o.l2_hot_bytes);
-  la.hints = o.l2_hot_bytes < 0 ? 0 : 1;
+
   la.alpha = (float)o.alpha;
   la.theta = (float)o.theta;
   la.ddof = o.znorm_ddof;
@@ -1027,12 +1417,17 @@ igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed
     la.stats_in = st_prev;
     la.stats_out = st;
     PhaseTimer pt(prof, IGP_PHASE_LAYER, s);
-    IGP_TRY(lops.layer(la, s));
+    IGP_TRY(tma ? lops.layer_tma(la, s) : lops.layer(la, s));
     cur = dst;
     st_prev = st;
   }
-  PhaseTimer pt(prof, IGP_PHASE_OUTPUT, s);
-  return ops.output(cur, g->dinv, st_prev, g->perm, N, dc, o.out_row_l2, out_dev, s);
+  {
+    PhaseTimer pt(prof, IGP_PHASE_OUTPUT, s);
+    IGP_TRY(ops.output(cur, g->dinv, st_prev, N, dc, o.out_row_l2, out_dev, s));
+  }
+  // the device error word of this call, read by igp_graph_sync / host-output calls
+  IGP_TRY_CUDA(cudaMemcpyAsync(g->err_host, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return IGP_OK;
 }
 
 }  // namespace igp
@@ -1144,27 +1539,31 @@ extern "C" igp_status igp_embed_noalloc(const int32_t* row_ptr, const int32_t* c
   float* stats = (float*)(base + 2 * bN + 2 * bT);
   long long* partials = (long long*)(base + 2 * bN + 2 * bT + bS);
   unsigned* ticket = (unsigned*)(base + 2 * bN + 2 * bT + bS + bP);
-  IGP_TRY_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s));
+  int* err = (int*)(ticket + 1);
+  IGP_TRY_CUDA(cudaMemsetAsync(ticket, 0, 2 * sizeof(unsigned), s));
 
   // the caller's graph as it is (no relabelling: that would need memory)
   IGP_TRY(launch_dinv_wsum(row_ptr, col, N, tau, o.eps, dinv, wsum, s));
   if (o.x_in) {
-    IGP_TRY(ops.prescale(o.x_in, dinv, nullptr, N, d, d, T0, s));
+    IGP_TRY(ops.prescale(o.x_in, dinv, N, d, d, T0, s));
   } else {
     const double xs = o.x_scale > 0 ? o.x_scale : 1.0 / std::sqrt((double)d);
-    IGP_TRY(launch_theta(seed, N, d, d, (float)xs, o.storage, dinv, nullptr, T0, s));
+    IGP_TRY(launch_theta(seed, N, d, d, (float)xs, o.storage, dinv, T0, s));
   }
   LayerArgs la;
   la.row_ptr = row_ptr;
   la.col = col;
+  la.perm = nullptr;  // rows in their own order
   la.dinv = dinv;
   la.wsum = wsum;
   la.partials = partials;
   la.tickets = ticket;
+  la.err = err;
+  la.withhold = 0;
+  la.gather4 = 0;
   la.N = N;
   la.d = d;
-  la.hot = hot_rows(N, d, sb, o.l2_hot_bytes);
-  la.hints = o.l2_hot_bytes < 0 ? 0 : 1;
+
   la.alpha = (float)o.alpha;
   la.theta = (float)o.theta;
   la.ddof = o.znorm_ddof;
@@ -1182,5 +1581,5 @@ extern "C" igp_status igp_embed_noalloc(const int32_t* row_ptr, const int32_t* c
     cur = dst;
     st_prev = st;
   }
-  return ops.output(cur, dinv, st_prev, nullptr, N, d, o.out_row_l2, out, s);
+  return ops.output(cur, dinv, st_prev, N, d, o.out_row_l2, out, s);
 }

@@ -77,17 +77,15 @@ struct igp_graph {
   // Eq. 1 factors for the last (tau, eps) asked for, and w_i = sum_{j in N(i)} dinv_j
   float* dinv = nullptr;       // device [N]
   float* wsum = nullptr;       // device [N], same allocation as dinv
-  // the graph relabelled by decreasing degree ("layer CSR"): layer row k is original row
-  // perm[k]; inv[perm[k]] = k; one allocation holds perm | inv | lrow_ptr
+  // rows in order of decreasing degree (the layer kernels' processing order)
   int32_t* perm = nullptr;
-  int32_t* inv = nullptr;
-  int32_t* lrow_ptr = nullptr;
-  int32_t* lcol = nullptr;
   double dinv_tau = 0, dinv_eps = 0;
   bool dinv_valid = false;
   // FFP workspace (grown on demand, kept until free)
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  // host copy (pinned) of the device error word of the last igp_embed
+  int* err_host = nullptr;
   // recorded on the stream of each call: later calls on another stream, and the
   // stream-ordered release in igp_graph_free, wait for it
   cudaEvent_t done = nullptr;
@@ -105,29 +103,29 @@ struct LayerArgs {
   const int32_t* col;
   const float* dinv;
   const float* wsum;
+  const int32_t* perm;  // processing order of the rows (NULL: their own order)
   const void* Tin;
   void* Tout;
   const float* stats_in;
   long long* partials;
   float* stats_out;
   unsigned* tickets;
-  int32_t N, d, hot;
-  int hints;
+  int* err;       // device word set to 1 by a layer whose bounded wait ran out
+  int withhold;   // test hook of the bounded wait (0 in normal use)
+  int gather4;    // bulk-copy kernel: 1 = tile::gather4 through a tensor map
+  int32_t N, d;
   float alpha, theta;
   int ddof, grid;
 };
 
 // ffp.cu
-igp_status ensure_layer_csr(igp_graph* g, cudaStream_t s);
-// dinv and w in layer-CSR order, for (tau, eps); builds the layer CSR on first use.
+igp_status ensure_perm(igp_graph* g, cudaStream_t s);
+// dinv and w for (tau, eps), cached on the graph.
 igp_status compute_dinv(igp_graph* g, double tau, double eps, cudaStream_t s, Profile* prof);
-// g's dinv (layer order) written in original node order into `out` (device).
-igp_status dinv_original_order(igp_graph* g, float* out, cudaStream_t s);
 // Theta (Alg. 1, line 2) into `out` in the storage type, in column blocks of dc columns
-// (dc = d: row-major), multiplied row-wise by dinv if non-NULL; row i holds the draw of
-// node rowid[i] (rowid NULL: node i).
+// (dc = d: row-major), multiplied row-wise by dinv if non-NULL.
 igp_status launch_theta(uint64_t seed, int32_t N, int32_t d, int32_t dc, float x_scale, int storage,
-                        const float* dinv, const int32_t* rowid, void* out, cudaStream_t s);
+                        const float* dinv, void* out, cudaStream_t s);
 igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed, float* out_dev,
                    const igp_embed_opts& o, cudaStream_t s);
 }  // namespace igp

@@ -283,3 +283,47 @@ def test_2m_config_full_size(api):
     assert float(z.mean(0).abs().max()) < 1e-2
     assert float((z.std(0) - 1).abs().max()) < 2e-2
     gr.free()
+
+
+# ---------------------------------------------------------------------------- gather modes
+@pytest.mark.parametrize("d,storage", [(64, "bf16"), (64, "f32"), (32, "bf16"), (128, "bf16"), (16, "f32")])
+def test_gather_modes_agree_bitwise(api, d, storage):
+    """Register-load and bulk-copy gathers add the same rows in the same order."""
+    import torch
+    g = synth.dcsbm(7001, 12, 22, 2.4, 5, seed=13)
+    gr = api.graph_build(g.src, g.dst, g.N)
+    outs = {}
+    for mode in ("lsu", "bulk", "tma4"):
+        o = torch.empty((g.N, d), dtype=torch.float32, device="cuda")
+        api.embed(gr, -0.5, 6, d, 9, out=o, storage=storage, gather=mode)
+        outs[mode] = o.cpu().numpy()
+    gr.sync()
+    gr.free()
+    assert np.array_equal(outs["lsu"], outs["bulk"])
+    assert np.array_equal(outs["lsu"], outs["tma4"])
+    rp, col = oracle.build_csr(g.src, g.dst, g.N)
+    ref = oracle.ffp(rp, col, oracle.theta_input(9, g.N, d), -0.5, 6)
+    assert row_rel_err(outs["lsu"], ref) <= TOL[storage]
+
+
+def test_bounded_device_wait_reports_timeout(api):
+    """A bulk-copy wait that cannot complete gives up after about a second: the host reads
+    IGP_E_TIMEOUT and the context stays usable (no trap, no hang)."""
+    import torch
+    g = synth.dcsbm(3000, 6, 16, 2.5, 5, seed=17)
+    gr = api.graph_build(g.src, g.dst, g.N)
+    out = torch.empty((g.N, 64), dtype=torch.float32, device="cuda")
+    api.embed(gr, -0.5, 2, 64, 1, out=out, storage="bf16", gather="bulk", reserved_test=1)
+    with pytest.raises(api.IgpError) as e:
+        gr.sync()
+    assert e.value.status == api.IGP_E_TIMEOUT
+    with pytest.raises(api.IgpError) as e:  # host output: reported by the call itself
+        api.embed(gr, -0.5, 1, 64, 1, storage="bf16", gather="tma4", reserved_test=1)
+    assert e.value.status == api.IGP_E_TIMEOUT
+    # the same handle and context work normally afterwards
+    api.embed(gr, -0.5, 3, 64, 2, out=out, storage="bf16", gather="tma4")
+    gr.sync()
+    rp, col = oracle.build_csr(g.src, g.dst, g.N)
+    ref = oracle.ffp(rp, col, oracle.theta_input(2, g.N, 64), -0.5, 3)
+    assert row_rel_err(out.cpu().numpy(), ref) <= TOL["bf16"]
+    gr.free()
