@@ -69,6 +69,7 @@ typedef int32_t igp_status;
 #define IGP_NUM_PHASES   5
 
 typedef struct igp_graph igp_graph;
+typedef struct igp_batch igp_batch;
 typedef struct igp_profile igp_profile;
 
 /* Options of one FFP. Fill with igp_embed_opts_init() and change fields. */
@@ -163,6 +164,37 @@ igp_status igp_generate_x(uint64_t seed, int32_t N, int32_t d, double x_scale, f
  */
 igp_status igp_embed(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed, float* out,
                      const igp_embed_opts* opts, void* stream);
+
+/*
+ * Batches: many independent graphs embedded together (block-diagonal packing). Each graph keeps its
+ * own Theta seed and its own ZNorm column statistics (Eq. 4 acts per graph), so every graph's
+ * result equals igp_embed on that graph alone, bit for bit.
+ *
+ * igp_batch_create: packs G built graphs (copied; the graphs may be freed afterwards) into one
+ *   device CSR, with each graph's rows by decreasing degree as the processing order. Synchronises
+ *   `stream`. Errors: IGP_E_INVAL (G < 1, NULL graph, more than 2^31 packed rows/entries), IGP_E_NOMEM.
+ */
+igp_status igp_batch_create(igp_graph* const* graphs, int32_t G, void* stream, igp_batch** out);
+
+/* G, total rows, total CSR entries, and (if row_offsets is non-NULL) the G+1 row offsets of the
+ * graphs in the packed output (host array). */
+igp_status igp_batch_info(const igp_batch* b, int32_t* G, int32_t* N_total, int64_t* nnz_total,
+                          int32_t* row_offsets);
+
+/*
+ * One FFP per graph of the batch (Alg. 1, lines 1-6), all graphs in the same launches:
+ *   seeds : host array of G Theta seeds (graph g's rows draw Theta with seeds[g] and local row ids)
+ *   out   : N_total x d fp32 (host or device); graph g's rows at row_offsets[g] ..
+ *   opts  : as igp_embed, except x_in, chunk_cols and TMA gathers (not supported here)
+ * With device output and no profile, the launch sequence is captured into a CUDA graph on first
+ * use and replayed while (tau, L, d, options, out) stay the same; the replay runs on a library
+ * stream ordered after, and before, the caller's `stream` by events.
+ */
+igp_status igp_batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uint64_t* seeds, float* out,
+                           const igp_embed_opts* opts, void* stream);
+
+/* Release a batch (waits for its work). NULL is a no-op. */
+void igp_batch_free(igp_batch* b);
 
 /*
  * igp_embed without any memory allocation. (The paper has no counterpart: this serves callers that

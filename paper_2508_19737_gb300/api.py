@@ -92,6 +92,15 @@ _SIGS = {
     "igp_embed_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p,
                                            ctypes.POINTER(EmbedOpts), ctypes.c_void_p]),
+    "igp_batch_create": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "igp_batch_info": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.c_void_p]),
+    "igp_batch_embed": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(EmbedOpts),
+                                         ctypes.c_void_p]),
+    "igp_batch_free": (None, [ctypes.c_void_p]),
     "igp_profile_create": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_void_p)]),
     "igp_profile_free": (None, [ctypes.c_void_p]),
     "igp_profile_read": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
@@ -303,3 +312,49 @@ def embed_noalloc(row_ptr, col, N, tau, L, d, seed, out, opts=None, stream=None,
     _check(lib().igp_embed_noalloc(_ptr(row_ptr), _ptr(col), int(N), float(tau), int(L), int(d),
                                    int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out), ctypes.byref(opts), _stream(stream)))
     return out
+
+
+class Batch:
+    """Owning wrapper of an igp_batch handle (many graphs embedded together)."""
+
+    def __init__(self, graphs, stream=None):
+        arr = (ctypes.c_void_p * len(graphs))(*[g.handle for g in graphs])
+        h = ctypes.c_void_p()
+        _check(lib().igp_batch_create(arr, len(graphs), _stream(stream), ctypes.byref(h)))
+        self.handle = h.value
+
+    def info(self):
+        G = ctypes.c_int32()
+        N = ctypes.c_int32()
+        nnz = ctypes.c_int64()
+        _check(lib().igp_batch_info(self.handle, ctypes.byref(G), ctypes.byref(N), ctypes.byref(nnz), None))
+        offs = np.empty(G.value + 1, dtype=np.int32)
+        _check(lib().igp_batch_info(self.handle, None, None, None, offs.ctypes.data))
+        return G.value, N.value, nnz.value, offs
+
+    def embed(self, tau, L, d, seeds, out=None, opts=None, stream=None, **kw):
+        """igp_batch_embed; seeds: G integers. Returns `out` (N_total x d)."""
+        if opts is None:
+            opts = embed_opts(**kw)
+        elif kw:
+            raise ValueError("give either opts or keyword options")
+        G, N, _, _ = self.info()
+        sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+        if sd.size != G:
+            raise ValueError("need one seed per graph")
+        if out is None:
+            out = np.empty((N, d), dtype=np.float32)
+        _check(lib().igp_batch_embed(self.handle, float(tau), int(L), int(d), sd.ctypes.data, _ptr(out),
+                                     ctypes.byref(opts), _stream(stream)))
+        return out
+
+    def free(self):
+        if self.handle:
+            lib().igp_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

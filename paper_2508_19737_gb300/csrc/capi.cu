@@ -403,6 +403,104 @@ igp_status igp_embed(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t se
   return st;
 }
 
+// ------------------------------------------------------------------ batches
+static void batch_release(igp_batch* b) {
+  if (!b) return;
+  if (b->cs) cudaStreamSynchronize(b->cs);
+  cudaDeviceSynchronize();
+  void* ptrs[] = {b->row_ptr, b->col, b->row_graph, b->perm, b->pgraph, b->goff, b->cost_pre, b->seeds_dev,
+                  b->dinv, b->part, b->ws};
+  for (void* q : ptrs)
+    if (q) cudaFreeAsync(q, 0);
+  cudaStreamSynchronize(0);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->cs) cudaStreamDestroy(b->cs);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  cudaGetLastError();
+  delete b;
+}
+
+igp_status igp_batch_create(igp_graph* const* graphs, int32_t G, void* stream, igp_batch** out) {
+  clear_error();
+  if (!out || !graphs || G < 1) {
+    set_error("igp_batch_create: need an output handle and G >= 1 graphs");
+    return IGP_E_INVAL;
+  }
+  *out = nullptr;
+  for (int32_t g = 0; g < G; ++g)
+    if (!graphs[g]) {
+      set_error("igp_batch_create: graph %d is NULL", g);
+      return IGP_E_INVAL;
+    }
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int32_t g = 0; g < G; ++g) IGP_TRY(graph_wait(graphs[g], s));
+  igp_batch* b = new (std::nothrow) igp_batch();
+  if (!b) return IGP_E_NOMEM;
+  cudaGetDevice(&b->device);
+  igp_status st = batch_create(graphs, G, s, b);
+  if (st != IGP_OK) {
+    batch_release(b);
+    return st;
+  }
+  *out = b;
+  return IGP_OK;
+}
+
+igp_status igp_batch_info(const igp_batch* b, int32_t* G, int32_t* N_total, int64_t* nnz_total,
+                          int32_t* row_offsets) {
+  clear_error();
+  if (!b) {
+    set_error("igp_batch_info: NULL batch");
+    return IGP_E_INVAL;
+  }
+  if (G) *G = b->G;
+  if (N_total) *N_total = b->N;
+  if (nnz_total) *nnz_total = b->nnz;
+  if (row_offsets) memcpy(row_offsets, b->goff_host.data(), (size_t)(b->G + 1) * sizeof(int32_t));
+  return IGP_OK;
+}
+
+igp_status igp_batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uint64_t* seeds, float* out,
+                           const igp_embed_opts* opts, void* stream) {
+  clear_error();
+  igp_embed_opts o;
+  if (opts)
+    o = *opts;
+  else
+    igp_embed_opts_init(&o);
+  if (!b || !seeds || !out) {
+    set_error("igp_batch_embed: NULL batch, seeds or output");
+    return IGP_E_INVAL;
+  }
+  if (!std::isfinite(tau) || L < 0 || L > 10000 || !std::isfinite(o.alpha) || !std::isfinite(o.theta) ||
+      !(o.eps > 0) || !std::isfinite(o.eps) || (o.znorm_ddof != 0 && o.znorm_ddof != 1) ||
+      (o.storage != IGP_STORE_F32 && o.storage != IGP_STORE_BF16) || !std::isfinite(o.x_scale)) {
+    set_error("igp_batch_embed: invalid tau, L or options");
+    return IGP_E_INVAL;
+  }
+  if (o.x_in || o.chunk_cols != 0 || (o.gather != IGP_GATHER_AUTO && o.gather != IGP_GATHER_LSU) ||
+      o.reserved_test) {
+    set_error("igp_batch_embed: x_in, chunk_cols, TMA gathers are not supported for batches");
+    return IGP_E_INVAL;
+  }
+  if (d != 8 && d != 16 && d != 32 && d != 64 && d != 128) {
+    set_error("igp_batch_embed: d=%d unsupported (8, 16, 32, 64, 128)", d);
+    return IGP_E_INVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (is_device_ptr(out)) return batch_embed(b, tau, L, d, seeds, out, o, s);
+  const size_t bytes = (size_t)b->N * d * sizeof(float);
+  void* tmp = nullptr;
+  IGP_TRY(dev_alloc(&tmp, bytes, s));
+  igp_status st = batch_embed(b, tau, L, d, seeds, (float*)tmp, o, s);
+  if (st == IGP_OK) st = copy_out(out, tmp, bytes, s);
+  dev_free(tmp, s);
+  return st;
+}
+
+void igp_batch_free(igp_batch* b) { batch_release(b); }
+
 igp_status igp_profile_create(igp_profile** p) {
   clear_error();
   if (!p) return IGP_E_INVAL;

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <string>
 #include <vector>
 
 #include "igp.h"
@@ -91,12 +92,46 @@ struct igp_graph {
   cudaEvent_t done = nullptr;
 };
 
+// Many graphs packed block-diagonally for one FFP each (igp_batch_*).
+struct igp_batch {
+  int32_t G = 0, N = 0;  // graphs, packed rows
+  int64_t nnz = 0, P = 0;  // packed CSR entries, processing-order length (padded)
+  int device = 0;
+  int32_t* row_ptr = nullptr;    // [N+1]
+  int32_t* col = nullptr;        // [nnz], packed ids
+  int32_t* row_graph = nullptr;  // [N] graph of each packed row
+  int32_t* perm = nullptr;       // [P] processing order: each graph's rows by decreasing degree, -1 padded
+  int32_t* pgraph = nullptr;     // [P/32] graph of each 32-position block of the order
+  int32_t* goff = nullptr;       // [G+1] packed row offset of each graph
+  int* cost_pre = nullptr;       // [P+1] work prefix over the order (warp partition)
+  std::vector<int32_t> goff_host;
+  uint64_t* seeds_dev = nullptr; // [G]
+  float* dinv = nullptr;         // [N], and w [N] after it
+  float* wsum = nullptr;
+  double dinv_tau = 0, dinv_eps = 0;
+  bool dinv_valid = false;
+  int32_t* part = nullptr;       // [nw+1] warp ranges of the order for nw warps
+  int64_t part_nw = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  // captured launch sequence and its parameters, replayed on cs
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::string exec_key;
+};
+
 namespace igp {
 // csr_build.cu: exclusive prefix sum of n >= 1 ints; tmp holds ceil(n / 8192) ints.
 igp_status exclusive_scan(const int* in, int* out, int64_t n, int* tmp, cudaStream_t s);
 // csr_build.cu: CSR of the undirected edge list (device inputs), into g (empty).
 igp_status build_csr(const int32_t* src, const int32_t* dst, int64_t M, int32_t N, cudaStream_t s,
                      igp_graph* g);
+// ffp.cu: batches
+igp_status batch_create(igp_graph* const* graphs, int32_t G, cudaStream_t s, igp_batch* b);
+igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uint64_t* seeds, float* out_dev,
+                       const igp_embed_opts& o, cudaStream_t s);
+
 // Arguments of one layer launch.
 struct LayerArgs {
   const int32_t* row_ptr;

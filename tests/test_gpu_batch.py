@@ -1,0 +1,97 @@
+"""Batches (block-diagonal packing of many graphs): every graph's result in the batch is
+bit-identical to igp_embed on that graph alone, and matches the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2508_19737_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-4, "bf16": 2e-2}
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_19737_gb300 import api as a
+    torch.cuda.set_device(0)
+    return a
+
+
+def _graphs():
+    gs = [synth.dcsbm(1000, 11, 20, 2.5, 10, seed=0),
+          synth.dcsbm(3001, 9, 16, 2.5, 6, seed=4),
+          synth.dcsbm(5000, 20, 30, 2.2, 5, seed=8)]
+    edges = [(g.src, g.dst, g.N) for g in gs]
+    edges.insert(1, (np.zeros(0, np.int32), np.zeros(0, np.int32), 1))        # a single node
+    edges.insert(3, (np.zeros(0, np.int32), np.zeros(0, np.int32), 50))       # edgeless
+    rng = np.random.default_rng(3)
+    edges.append((rng.integers(0, 17, 30).astype(np.int32), rng.integers(0, 17, 30).astype(np.int32), 17))
+    return edges
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)))
+
+
+@pytest.mark.parametrize("d,storage", [(64, "bf16"), (32, "f32"), (16, "bf16")])
+def test_batch_equals_each_graph_alone(api, d, storage):
+    import torch
+    edges = _graphs()
+    graphs = [api.graph_build(s, t, n) for s, t, n in edges]
+    batch = api.Batch(graphs)
+    G, N, nnz, offs = batch.info()
+    assert G == len(edges) and N == sum(n for _, _, n in edges)
+    assert nnz == sum(g.nnz for g in graphs)
+    seeds = [11 * k + 1 for k in range(G)]
+    out = torch.empty((N, d), dtype=torch.float32, device="cuda")
+    for rep in range(2):  # second call replays the captured launch sequence
+        out.fill_(-1.0)
+        batch.embed(-0.5, 6, d, seeds, out=out, storage=storage)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        for k, (g, (s, t, n)) in enumerate(zip(graphs, edges)):
+            alone = api.embed(g, -0.5, 6, d, seeds[k], storage=storage)
+            assert np.array_equal(got[offs[k]:offs[k + 1]], alone), (rep, k)
+    # against the oracle on two of the graphs
+    for k in (0, 4):
+        s, t, n = edges[k]
+        rp, col = oracle.build_csr(s, t, n)
+        ref = oracle.ffp(rp, col, oracle.theta_input(seeds[k], n, d), -0.5, 6)
+        assert _rel(got[offs[k]:offs[k + 1]], ref) <= TOL[storage]
+    # new seeds on the same captured sequence
+    seeds2 = [7 * k + 3 for k in range(G)]
+    batch.embed(-0.5, 6, d, seeds2, out=out, storage=storage)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for k in (0, 2, 5):
+        alone = api.embed(graphs[k], -0.5, 6, d, seeds2[k], storage=storage)
+        assert np.array_equal(got[offs[k]:offs[k + 1]], alone)
+    batch.free()
+    for g in graphs:
+        g.free()
+
+
+def test_batch_host_output_and_options(api):
+    edges = _graphs()[:3]
+    graphs = [api.graph_build(s, t, n) for s, t, n in edges]
+    batch = api.Batch(graphs)
+    for g in graphs:  # the batch holds its own copy
+        g.free()
+    out = batch.embed(-1.0, 4, 32, [5, 6, 7], znorm_ddof=0, alpha=-0.5, theta=0.7, out_row_l2=True)
+    G, N, _, offs = batch.info()
+    s, t, n = edges[0]
+    rp, col = oracle.build_csr(s, t, n)
+    ref = oracle.ffp(rp, col, oracle.theta_input(5, n, 32), -1.0, 4, ddof=0, alpha=-0.5, theta=0.7,
+                     out_row_l2=True)
+    assert _rel(out[offs[0]:offs[1]], ref) <= TOL["f32"]
+    with pytest.raises(api.IgpError):
+        batch.embed(-0.5, 2, 32, [1, 2, 3], chunk_cols=16)
+    with pytest.raises(ValueError):
+        batch.embed(-0.5, 2, 32, [1, 2])
+    batch.free()
