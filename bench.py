@@ -42,7 +42,8 @@ def parse():
     p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="dcsbm-2m", choices=sorted(synth.WORKLOADS))
+    p.add_argument("--workload", default="dcsbm-2m", choices=sorted(synth.WORKLOADS) + sorted(synth.BATCH_WORKLOADS))
+    p.add_argument("--d", type=int, default=None, help="override the workload's embedding width")
     p.add_argument("--storage", default=None, choices=[None, "f32", "bf16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=None)
@@ -213,11 +214,105 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- batches
+def run_batch(args):
+    """Many graphs embedded together (igp_batch_embed, CUDA-graph replay) against the same
+    graphs embedded one after another in fp32 (igp_embed per graph). A step is one FFP of
+    every graph; the graphs are built and packed once, before timing."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_19737_gb300 import api
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    wl = synth.BATCH_WORKLOADS[args.workload]
+    storage = args.storage or wl["storage"]
+    sb = 2 if storage == "bf16" else 4
+    d = args.d or wl["d"]
+    tau, L = wl["tau"], wl["L"]
+    gs = synth.workload_batch(args.workload)
+    graphs = [api.graph_build(torch.from_numpy(g.src).cuda(), torch.from_numpy(g.dst).cuda(), g.N) for g in gs]
+    batch = api.Batch(graphs)
+    G, N, nnz, offs = batch.info()
+    seeds = list(range(G))
+    out = torch.empty((N, d), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    opts = api.embed_opts(storage=storage)
+    for _ in range(max(args.warmup, 3)):
+        batch.embed(tau, L, d, seeds, out=out, opts=opts, stream=stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    n0 = api.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        batch.embed(tau, L, d, seeds, out=out, opts=opts, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = api.launch_count() - n0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    units = float(nnz) * d * L
+    value = units * args.steps / (ms / 1e3)
+    # per-launch layer time (plain launches with events)
+    prof = api.Profile()
+    popts = api.embed_opts(storage=storage, profile=prof)
+    batch.embed(tau, L, d, seeds, out=out, opts=popts, stream=stream)
+    torch.cuda.synchronize()
+    ph = prof.read()
+    prof.close()
+    layer_s = ph["layer"][0] / max(ph["layer"][1], 1) / 1e3
+    lb = layer_bytes(N, nnz, d, sb)
+    peak, peak_src = peaks()
+    # the same graphs one at a time, fp32
+    seq_out = [torch.empty((g.N, d), dtype=torch.float32, device="cuda") for g in gs]
+    sopts = api.embed_opts(storage="f32")
+    for k, g in enumerate(graphs):
+        api.embed(g, tau, L, d, seeds[k], out=seq_out[k], opts=sopts, stream=stream)
+    torch.cuda.synchronize()
+    reps = 2
+    e0.record(stream)
+    for _ in range(reps):
+        for k, g in enumerate(graphs):
+            api.embed(g, tau, L, d, seeds[k], out=seq_out[k], opts=sopts, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1) / reps
+    seq_value = units / (seq_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": storage, "data": "synthetic",
+        "config": {"workload": args.workload, **wl["batch"], "N_total": N, "nnz_total": int(nnz), "d": d,
+                   "tau": tau, "L": L, "storage": storage, "accumulate": "f32",
+                   "step": "igp_batch_embed of all graphs (CUDA-graph replay); graphs built and packed once",
+                   "l2": "inputs larger than L2" if N * d * sb > L2_BYTES else "working set may fit L2"},
+        "roofline": {"bound": "hbm", "achieved": lb / layer_s / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": lb / layer_s / 1e9 / peak, "traffic": None, "kernel": "k_layer_batch",
+                     "avg_launch_ms": layer_s * 1e3, "algorithmic_bytes_per_launch": lb},
+        "sequential_fp32": {"value": seq_value, "unit": UNIT, "ms_per_pass": seq_ms,
+                            "what": "igp_embed of each graph in turn, fp32 storage, same d, tau, L, seeds"},
+        "speedup_vs_sequential_fp32": value / seq_value,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    batch.free()
+    return 0
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in synth.BATCH_WORKLOADS:
+        return run_batch(args)
     import torch
     import torch.distributed as dist
 

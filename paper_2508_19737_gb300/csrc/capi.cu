@@ -408,8 +408,7 @@ static void batch_release(igp_batch* b) {
   if (!b) return;
   if (b->cs) cudaStreamSynchronize(b->cs);
   cudaDeviceSynchronize();
-  void* ptrs[] = {b->row_ptr, b->col, b->row_graph, b->perm, b->pgraph, b->goff, b->cost_pre, b->seeds_dev,
-                  b->dinv, b->part, b->ws};
+  void* ptrs[] = {b->row_ptr, b->col, b->row_graph, b->perm, b->pgraph, b->goff, b->seeds_dev, b->dinv, b->ws};
   for (void* q : ptrs)
     if (q) cudaFreeAsync(q, 0);
   cudaStreamSynchronize(0);

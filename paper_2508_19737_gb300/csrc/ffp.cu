@@ -1016,6 +1016,7 @@ __global__ void k_output(const S* __restrict__ T, const float* __restrict__ dinv
 // The processing order lists each graph's rows by decreasing degree, padded with -1 to
 // a multiple of kBatchAlign, so a warp tile never mixes graphs.
 constexpr int kBatchAlign = 32;
+constexpr int kBatchChunk = 64;  // order positions per warp turn (a multiple of kBatchAlign)
 
 struct PackSrc {
   const int32_t* row_ptr;  // graph's own CSR
@@ -1042,41 +1043,6 @@ __global__ void k_batch_pack(const PackSrc* __restrict__ src, int32_t G, int32_t
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < P; k += stride) {
     perm[ps.poff + k] = k < ps.N ? ps.roff + ps.perm[k] : -1;
     if (k % kBatchAlign == 0) pgraph[(ps.poff + k) / kBatchAlign] = g;
-  }
-}
-
-// cost[p] = work of order position p (CSR entries + a per-row cost), cost[P] = 0
-__global__ void k_batch_cost(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ perm, int64_t P,
-                             int* __restrict__ cost) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= P; p += (int64_t)gridDim.x * blockDim.x) {
-    int c = 0;
-    if (p < P) {
-      const int r = perm[p];
-      if (r >= 0) c = row_ptr[r + 1] - row_ptr[r] + 4;
-    }
-    cost[p] = c;
-  }
-}
-
-// part[w] = first order position whose cost prefix reaches w * total / nw, rounded down to
-// a multiple of kBatchAlign; part[nw] = P. Warp w takes positions [part[w], part[w+1]).
-__global__ void k_batch_partition(const int* __restrict__ pre, int64_t P, int64_t nw, int32_t* __restrict__ part) {
-  const int64_t total = pre[P];
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w <= nw; w += (int64_t)gridDim.x * blockDim.x) {
-    if (w == nw) {
-      part[w] = (int32_t)P;
-      continue;
-    }
-    const int64_t target = total * w / nw;
-    int64_t lo = 0, hi = P;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (pre[mid] < target)
-        lo = mid + 1;
-      else
-        hi = mid;
-    }
-    part[w] = (int32_t)(lo / kBatchAlign * kBatchAlign);
   }
 }
 
@@ -1109,16 +1075,19 @@ __global__ void k_theta_batch(const uint64_t* __restrict__ seeds, const int32_t*
   }
 }
 
-// One Eq. 4 layer over a batch: the gather/epilogue of k_layer; warp w walks its
-// contiguous order range [part[w], part[w+1]) tile by tile; the column statistics are
-// kept per graph (exact int64 sums, atomically added to gsum[g] when a warp leaves a
-// graph) and finished by k_batch_stats.
+// One Eq. 4 layer over a batch: the gather/epilogue of k_layer. The processing order is
+// cut into chunks of kBatchChunk positions that warps claim in order from a global
+// counter, so at any time the GPU works on a narrow window of the order, i.e. on a few
+// graphs, whose rows (the only ones their neighbours can be) stay in L2; claiming also
+// balances the load. (Which warp takes which rows changes nothing in the result.) The column statistics are kept per graph
+// (exact int64 sums, added atomically to gsum[g] when a warp leaves a graph) and finished
+// by k_batch_stats.
 template <int D, typename S>
 __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer_batch(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const float* __restrict__ dinv,
-    const float* __restrict__ wsum, const int32_t* __restrict__ perm, const int32_t* __restrict__ pgraph,
-    const int32_t* __restrict__ part, const S* __restrict__ Tin, S* __restrict__ Tout_all,
-    const float* __restrict__ stats_in, unsigned long long* __restrict__ gsum, float alpha, float theta) {
+    const float* __restrict__ wsum, const int32_t* __restrict__ perm, const int32_t* __restrict__ pgraph, int64_t P,
+    const S* __restrict__ Tin, S* __restrict__ Tout_all, const float* __restrict__ stats_in,
+    unsigned long long* __restrict__ gsum, unsigned* __restrict__ chunk_ctr, float alpha, float theta) {
   using RW = Raw<S>;
   using RT = typename RW::T;
   constexpr int VPL = Store<S>::VPL;
@@ -1133,8 +1102,22 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer_bat
   const int grp = lane / G, lig = lane % G;
   S* __restrict__ Tout = Tout_all + lig * VPL;
   const uint64_t pol_first = evict_first_policy();
-  const int64_t w = (int64_t)blockIdx.x * kLayerWarps + warp;
-  const int p0 = part[w], p1 = part[w + 1];
+  // chunks claimed by this warp, one claim ahead of use
+  auto claim = [&]() -> int64_t {
+    unsigned c = 0;
+    if (lane == 0) c = atomicAdd(chunk_ctr, 1u);
+    return (int64_t)__shfl_sync(0xffffffffu, c, 0) * kBatchChunk;
+  };
+  int64_t next_chunk = claim();
+  auto next_pos = [&](int64_t p) -> int64_t {
+    const int64_t q = p + GPW;
+    if (q % kBatchChunk) return q;
+    const int64_t c = next_chunk;
+    next_chunk = claim();
+    return c;
+  };
+  const int64_t p0 = next_chunk;
+  next_chunk = claim();
 
   long long qs[VPL], qq[VPL];
 #pragma unroll
@@ -1172,7 +1155,7 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer_bat
     RT self;
     float di, wi;
   };
-  auto row_at = [&](int p) -> int { return p < p1 ? __ldg(perm + p + grp) : -1; };
+  auto row_at = [&](int64_t p) -> int { return p < P ? __ldg(perm + p + grp) : -1; };
   auto fetch_row = [&](int r, RowData& rd) {
     if (r >= 0) {
       rd.b = __ldg(row_ptr + r);
@@ -1189,10 +1172,12 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer_bat
   int r = row_at(p0);
   RowData cur;
   fetch_row(r, cur);
-  int r_n = row_at(p0 + GPW);
+  int64_t pn = next_pos(p0);
+  int r_n = row_at(pn);
   int jw[IPL];
   load_idx(jw, cur.b, cur.e);
-  for (int p = p0; p < p1; p += GPW) {
+  for (int64_t p = p0; p < P;) {
+    const int64_t pnn = next_pos(pn);  // (claims a chunk at a boundary: call once per step)
     const int g = __ldg(pgraph + p / kBatchAlign);
     if (g != cur_g) {  // warp-uniform: a tile belongs to one graph
       flush();
@@ -1203,7 +1188,7 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer_bat
       }
       __syncwarp();
     }
-    const int r_nn = row_at(p + 2 * GPW);
+    const int r_nn = row_at(pnn);
     RowData nxt;
     fetch_row(r_n, nxt);
     const int mtrip = __reduce_max_sync(0xffffffffu, (cur.e - cur.b + C - 1) / C);
@@ -1250,6 +1235,8 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer_bat
     r = r_n;
     r_n = r_nn;
     cur = nxt;
+    p = pn;
+    pn = pnn;
   }
   flush();
 }
@@ -1257,7 +1244,8 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer_bat
 // Per graph and column: mean and 1/std from the exact sums (then cleared for the next layer).
 template <int D>
 __global__ void k_batch_stats(unsigned long long* __restrict__ gsum, const int32_t* __restrict__ goff, int32_t G,
-                              int ddof, float* __restrict__ stats_out) {
+                              int ddof, float* __restrict__ stats_out, unsigned* __restrict__ chunk_ctr) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *chunk_ctr = 0u;  // for the next layer
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)G * D;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int g = (int)(t / D), c = (int)(t - (int64_t)g * D);
@@ -1488,7 +1476,8 @@ template <int D, typename S>
 igp_status batch_layer_launch(const igp_batch* b, const void* Tin, void* Tout, const float* st_in,
                               unsigned long long* gsum, float alpha, float theta, int grid, cudaStream_t s) {
   k_layer_batch<D, S><<<grid, kLayerThreads, 0, s>>>(b->row_ptr, b->col, b->dinv, b->wsum, b->perm, b->pgraph,
-                                                     b->part, (const S*)Tin, (S*)Tout, st_in, gsum, alpha, theta);
+                                                     b->P, (const S*)Tin, (S*)Tout, st_in, gsum,
+                                                     (unsigned*)(gsum + (int64_t)b->G * 2 * D), alpha, theta);
   return after_launch("k_layer_batch");
 }
 
@@ -1496,7 +1485,8 @@ template <int D, typename S>
 igp_status batch_tail_launch(const igp_batch* b, unsigned long long* gsum, int ddof, float* st_out, cudaStream_t s) {
   const int64_t n = (int64_t)b->G * D;
   const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
-  k_batch_stats<D><<<std::max(blocks, 1), 256, 0, s>>>(gsum, b->goff, b->G, ddof, st_out);
+  k_batch_stats<D><<<std::max(blocks, 1), 256, 0, s>>>(gsum, b->goff, b->G, ddof, st_out,
+                                                        (unsigned*)(gsum + (int64_t)b->G * 2 * D));
   return after_launch("k_batch_stats");
 }
 
@@ -1797,7 +1787,7 @@ igp_status batch_create(igp_graph* const* graphs, int32_t G, cudaStream_t s, igp
   b->nnz = nnz;
   b->P = P;
   auto alloc = [&](void** p, size_t bytes) { return dev_alloc(p, bytes, s); };
-  void *rp, *cl, *rg, *pm, *pg, *go, *cp, *sd, *ps;
+  void *rp, *cl, *rg, *pm, *pg, *go, *sd, *ps;
   IGP_TRY(alloc(&rp, (N + 1) * 4));
   b->row_ptr = (int32_t*)rp;
   IGP_TRY(alloc(&cl, std::max<int64_t>(nnz, 1) * 4));
@@ -1810,8 +1800,6 @@ igp_status batch_create(igp_graph* const* graphs, int32_t G, cudaStream_t s, igp
   b->pgraph = (int32_t*)pg;
   IGP_TRY(alloc(&go, (G + 1) * 4));
   b->goff = (int32_t*)go;
-  IGP_TRY(alloc(&cp, (P + 1) * 4));
-  b->cost_pre = (int*)cp;
   IGP_TRY(alloc(&sd, (size_t)G * 8));
   b->seeds_dev = (uint64_t*)sd;
   IGP_TRY(alloc(&ps, (size_t)G * sizeof(PackSrc)));
@@ -1822,15 +1810,6 @@ igp_status batch_create(igp_graph* const* graphs, int32_t G, cudaStream_t s, igp
   dim3 grid(std::max(1, num_sms() * 4 / std::max(G, 1)), G);
   k_batch_pack<<<grid, 256, 0, s>>>((const PackSrc*)ps, G, b->row_ptr, b->col, b->row_graph, b->perm, b->pgraph);
   IGP_TRY(after_launch("k_batch_pack"));
-  // work prefix over the processing order, for the warp partition of each launch size
-  void* t = nullptr;
-  const int64_t ntiles = (P + 1 + 8191) / 8192;
-  IGP_TRY(alloc(&t, (P + 1 + ntiles) * 4));
-  const int blocks = (int)std::min<int64_t>((P + 1 + 255) / 256, (int64_t)num_sms() * 8);
-  k_batch_cost<<<std::max(blocks, 1), 256, 0, s>>>(b->row_ptr, b->perm, P, (int*)t);
-  IGP_TRY(after_launch("k_batch_cost"));
-  IGP_TRY(exclusive_scan((int*)t, b->cost_pre, P + 1, (int*)t + (P + 1), s));
-  dev_free(t, s);
   IGP_TRY_CUDA(cudaStreamSynchronize(s));  // the host arrays above and the source graphs are read
   dev_free(ps, s);
   return IGP_OK;
@@ -1862,26 +1841,14 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
     b->dinv_eps = o.eps;
     b->exec_key.clear();
   }
-  // warp partition for this launch size
-  const int64_t want = (b->P + kLayerWarps * 64 - 1) / (kLayerWarps * 64);
+  // one full wave of CTAs, each warp taking chunks of the order grid-stride
+  const int64_t want = (b->P + kLayerWarps * kBatchChunk - 1) / (kLayerWarps * kBatchChunk);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)bo.per_sm() * num_sms()));
-  const int64_t nw = (int64_t)grid * kLayerWarps;
-  if (b->part_nw != nw) {
-    if (b->part) dev_free(b->part, s);
-    void* p = nullptr;
-    IGP_TRY(dev_alloc(&p, (size_t)(nw + 1) * 4, s));
-    b->part = (int32_t*)p;
-    const int blocks = (int)std::min<int64_t>((nw + 1 + 255) / 256, (int64_t)num_sms() * 4);
-    k_batch_partition<<<std::max(blocks, 1), 256, 0, s>>>(b->cost_pre, b->P, nw, b->part);
-    IGP_TRY(after_launch("k_batch_partition"));
-    b->part_nw = nw;
-    b->exec_key.clear();
-  }
   // workspace: T0 | T1 | stats[2][G][2d] | gsum[G][2d]
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t bT = al((size_t)N * d * sb);
   const size_t bS = al((size_t)2 * G * 2 * d * sizeof(float));
-  const size_t bQ = al((size_t)G * 2 * d * sizeof(unsigned long long));
+  const size_t bQ = al((size_t)G * 2 * d * sizeof(unsigned long long) + sizeof(unsigned long long));  // + counter
   const size_t need = 2 * bT + bS + bQ;
   if (b->ws_bytes < need) {
     if (b->ws) dev_free(b->ws, s);

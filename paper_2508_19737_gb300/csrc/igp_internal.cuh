@@ -103,15 +103,12 @@ struct igp_batch {
   int32_t* perm = nullptr;       // [P] processing order: each graph's rows by decreasing degree, -1 padded
   int32_t* pgraph = nullptr;     // [P/32] graph of each 32-position block of the order
   int32_t* goff = nullptr;       // [G+1] packed row offset of each graph
-  int* cost_pre = nullptr;       // [P+1] work prefix over the order (warp partition)
   std::vector<int32_t> goff_host;
   uint64_t* seeds_dev = nullptr; // [G]
   float* dinv = nullptr;         // [N], and w [N] after it
   float* wsum = nullptr;
   double dinv_tau = 0, dinv_eps = 0;
   bool dinv_valid = false;
-  int32_t* part = nullptr;       // [nw+1] warp ranges of the order for nw warps
-  int64_t part_nw = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
   // captured launch sequence and its parameters, replayed on cs

@@ -247,5 +247,19 @@ WORKLOADS = {
 }
 
 
+# 512 independent graphs, N log-uniform on [1,000, 50,000], blocks round(N^0.4), mean degree
+# uniform on [10, 40], gamma 2.5, ratio 5 (embedded together as one batch)
+BATCH_WORKLOADS = {
+    "dcsbm-batch512": dict(batch=dict(G=512, n_lo=1000, n_hi=50000, deg_lo=10, deg_hi=40, gamma=2.5, ratio=5,
+                                      seed=0),
+                           d=64, tau=-0.5, L=10, storage="bf16"),
+}
+
+
 def workload_graph(name):
     return dcsbm(**WORKLOADS[name]["graph"])
+
+
+def workload_batch(name):
+    b = BATCH_WORKLOADS[name]["batch"]
+    return batch_dcsbm(b["G"], b["n_lo"], b["n_hi"], b["deg_lo"], b["deg_hi"], b["gamma"], b["ratio"], seed=b["seed"])
