@@ -122,6 +122,17 @@ igp_status igp_graph_build(const int32_t* src, const int32_t* dst, int64_t M, in
 igp_status igp_graph_build_profiled(const int32_t* src, const int32_t* dst, int64_t M, int32_t N,
                                     void* stream, igp_profile* profile, igp_graph** out);
 
+/*
+ * Streaming update (Alg. 2, lines 1-2): merge an increment of undirected edges into the graph's
+ * device-resident CSR, growing it to N_new >= N nodes (new nodes start without edges). The result
+ * is the CSR igp_graph_build would give for all edges so far and N_new (sorted, deduplicated,
+ * no self-loops). Cached per-graph state (degree factors, processing order) is refreshed on the
+ * next use. Errors: IGP_E_INVAL (N_new < N, id outside [0, N_new); the graph is then unchanged),
+ * IGP_E_NOMEM, IGP_E_CUDA. Synchronises `stream` once.
+ */
+igp_status igp_graph_append(igp_graph* g, const int32_t* src, const int32_t* dst, int64_t M_new, int32_t N_new,
+                            void* stream);
+
 /* N, number of stored (directed) CSR entries nnz = sum of degrees, and the largest degree. */
 igp_status igp_graph_info(const igp_graph* g, int32_t* N, int64_t* nnz, int32_t* max_deg);
 

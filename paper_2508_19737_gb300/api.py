@@ -78,6 +78,8 @@ _SIGS = {
                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "igp_graph_build_profiled": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "igp_graph_append": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_int32, ctypes.c_void_p]),
     "igp_graph_info": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
     "igp_graph_export": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -236,6 +238,13 @@ class Graph:
             col = np.empty(nnz, dtype=np.int32)
         _check(lib().igp_graph_export(self.handle, _ptr(row_ptr), _ptr(col), _stream(stream)))
         return row_ptr, col
+
+    def append(self, src, dst, N_new, stream=None):
+        """igp_graph_append: merge an edge increment (int32 arrays, host or device), growing to N_new."""
+        M = int(src.shape[0])
+        if int(dst.shape[0]) != M:
+            raise ValueError("src and dst differ in length")
+        _check(lib().igp_graph_append(self.handle, _ptr(src), _ptr(dst), M, int(N_new), _stream(stream)))
 
     def sync(self):
         """igp_graph_sync: wait for the handle's work; raises IgpError(IGP_E_TIMEOUT) if a

@@ -239,6 +239,27 @@ igp_status igp_graph_build(const int32_t* src, const int32_t* dst, int64_t M, in
   return igp_graph_build_profiled(src, dst, M, N, stream, nullptr, out);
 }
 
+igp_status igp_graph_append(igp_graph* g, const int32_t* src, const int32_t* dst, int64_t M_new, int32_t N_new,
+                            void* stream) {
+  clear_error();
+  if (!g || N_new < g->N || N_new >= 2147483647 || M_new < 0 || M_new >= (1LL << 30) ||
+      (M_new > 0 && (!src || !dst))) {
+    set_error("igp_graph_append: need a graph, N_new >= its N (N_new < 2^31-1), 0 <= M_new < 2^30 and edge arrays");
+    return IGP_E_INVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  IGP_TRY(graph_wait(g, s));
+  const void *ds = nullptr, *dd = nullptr;
+  void *os = nullptr, *od = nullptr;
+  igp_status st = to_device(src, (size_t)M_new * sizeof(int32_t), s, &ds, &os);
+  if (st == IGP_OK) st = to_device(dst, (size_t)M_new * sizeof(int32_t), s, &dd, &od);
+  if (st == IGP_OK) st = append_csr(g, (const int32_t*)ds, (const int32_t*)dd, M_new, N_new, s);
+  dev_free(os, s);
+  dev_free(od, s);
+  if (st == IGP_OK) st = graph_mark(g, s);
+  return st;
+}
+
 igp_status igp_graph_info(const igp_graph* g, int32_t* N, int64_t* nnz, int32_t* max_deg) {
   clear_error();
   if (!g) {

@@ -348,6 +348,76 @@ __global__ void k_compact(const int* __restrict__ off, const int32_t* __restrict
   }
 }
 
+// ------------------------------------------------------------------ streaming merge
+// Union of the sorted, duplicate-free rows of the old CSR (rows < N_old) and of the
+// increment's CSR (N_new rows), one warp per row. Pass 1 drops from each increment row
+// the columns the old row already has (compacting the increment row in place, in order)
+// and counts the union; pass 2 merges the two now disjoint sorted lists: an element's
+// place is its index in its own list plus the number of smaller elements of the other.
+__device__ __forceinline__ int lower_bound_dev(const int32_t* a, int n, int32_t x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < x)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_merge_count(const int32_t* __restrict__ rp_a, const int32_t* __restrict__ col_a, int32_t N_old,
+                              const int32_t* __restrict__ rp_b, int32_t* col_b, int32_t N_new, int* __restrict__ cnt,
+                              int* __restrict__ nbp, int* __restrict__ max_deg) {
+  const int lane = threadIdx.x & 31;
+  int local_max = 0;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < N_new;
+       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int32_t* A = col_a + (i < N_old ? rp_a[i] : 0);
+    const int na = i < N_old ? rp_a[i + 1] - rp_a[i] : 0;
+    int32_t* B = col_b + rp_b[i];
+    const int nb = rp_b[i + 1] - rp_b[i];
+    int base = 0;
+    for (int c = 0; c < nb; c += 32) {
+      const int k = c + lane;
+      const bool valid = k < nb;
+      const int32_t x = valid ? B[k] : 0;
+      bool keep = false;
+      if (valid) {
+        const int r = lower_bound_dev(A, na, x);
+        keep = !(r < na && A[r] == x);
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, keep);  // all reads of the chunk precede the writes
+      if (keep) B[base + __popc(m & lanemask_lt())] = x;
+      base += __popc(m);
+    }
+    const int n = na + base;
+    if (lane == 0) {
+      cnt[i] = n;
+      nbp[i] = base;
+    }
+    local_max = max(local_max, n);
+  }
+  if (lane == 0 && local_max > 0) atomicMax(max_deg, local_max);
+}
+
+__global__ void k_merge_write(const int32_t* __restrict__ rp_a, const int32_t* __restrict__ col_a, int32_t N_old,
+                              const int32_t* __restrict__ rp_b, const int32_t* __restrict__ col_b,
+                              const int* __restrict__ nbp, int32_t N_new, const int32_t* __restrict__ rp_out,
+                              int32_t* __restrict__ col_out) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < N_new;
+       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int32_t* A = col_a + (i < N_old ? rp_a[i] : 0);
+    const int na = i < N_old ? rp_a[i + 1] - rp_a[i] : 0;
+    const int32_t* B = col_b + rp_b[i];
+    const int nb = nbp[i];
+    const int o = rp_out[i];
+    for (int k = lane; k < na; k += 32) col_out[o + k + lower_bound_dev(B, nb, A[k])] = A[k];
+    for (int k = lane; k < nb; k += 32) col_out[o + k + lower_bound_dev(A, na, B[k])] = B[k];
+  }
+}
+
 }  // namespace
 
 igp_status build_csr(const int32_t* src, const int32_t* dst, int64_t M, int32_t N, cudaStream_t s, igp_graph* g) {
@@ -461,6 +531,77 @@ igp_status build_csr(const int32_t* src, const int32_t* dst, int64_t M, int32_t 
   g->col = col;
   return IGP_OK;
 #undef STEP
+}
+
+// Alg. 2, lines 1-2: merge an increment of edges (and new nodes up to N_new) into g.
+igp_status append_csr(igp_graph* g, const int32_t* src, const int32_t* dst, int64_t M, int32_t N_new, cudaStream_t s) {
+  igp_graph inc;
+  IGP_TRY(build_csr(src, dst, M, N_new, s, &inc));  // validates ids, sorts and dedups the increment
+  const int64_t n1 = (int64_t)N_new + 1;
+  const int64_t ntiles = (n1 + kScanTile - 1) / kScanTile;
+  void* t = nullptr;
+  igp_status st = dev_alloc(&t, (size_t)(2 * n1 + ntiles + 1) * sizeof(int), s);
+  if (st != IGP_OK) {
+    dev_free(inc.row_ptr, s);
+    dev_free(inc.col, s);
+    return st;
+  }
+  int* cnt = (int*)t;
+  int* nbp = cnt + n1;
+  int* tiles = nbp + n1;
+  int* max_deg = tiles + ntiles;
+  int32_t* rp = nullptr;
+  int32_t* col = nullptr;
+  int host_nnz = 0, host_max = 0;
+  auto cleanup = [&](igp_status e) {
+    dev_free(t, s);
+    dev_free(inc.row_ptr, s);
+    dev_free(inc.col, s);
+    if (e != IGP_OK) {
+      dev_free(rp, s);
+      dev_free(col, s);
+    }
+    return e;
+  };
+  if (cudaMemsetAsync(cnt + N_new, 0, sizeof(int), s) != cudaSuccess ||
+      cudaMemsetAsync(max_deg, 0, sizeof(int), s) != cudaSuccess)
+    return cleanup(cuda_status(cudaGetLastError(), "memset", __FILE__, __LINE__));
+  const int blocks = (int)std::min<int64_t>((n1 * 32 + 255) / 256, (int64_t)num_sms() * 16);
+  k_merge_count<<<blocks, 256, 0, s>>>(g->row_ptr, g->col, g->N, inc.row_ptr, inc.col, N_new, cnt, nbp, max_deg);
+  if ((st = after_launch("k_merge_count")) != IGP_OK) return cleanup(st);
+  {
+    void* p = nullptr;
+    if ((st = dev_alloc(&p, n1 * sizeof(int32_t), s)) != IGP_OK) return cleanup(st);
+    rp = (int32_t*)p;
+  }
+  if ((st = exclusive_scan(cnt, rp, n1, tiles, s)) != IGP_OK) return cleanup(st);
+  if (cudaMemcpyAsync(&host_nnz, rp + N_new, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&host_max, max_deg, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return cleanup(cuda_status(cudaGetLastError(), "igp_graph_append readback", __FILE__, __LINE__));
+  {
+    void* p = nullptr;
+    if ((st = dev_alloc(&p, (size_t)std::max(host_nnz, 1) * sizeof(int32_t), s)) != IGP_OK) return cleanup(st);
+    col = (int32_t*)p;
+  }
+  k_merge_write<<<blocks, 256, 0, s>>>(g->row_ptr, g->col, g->N, inc.row_ptr, inc.col, nbp, N_new, rp, col);
+  if ((st = after_launch("k_merge_write")) != IGP_OK) return cleanup(st);
+  cleanup(IGP_OK);
+  dev_free(g->row_ptr, s);
+  dev_free(g->col, s);
+  g->row_ptr = rp;
+  g->col = col;
+  g->nnz = host_nnz;
+  g->max_deg = host_max;
+  if (N_new != g->N) {  // per-node arrays change size
+    dev_free(g->dinv, s);
+    g->dinv = g->wsum = nullptr;
+  }
+  g->N = N_new;
+  g->dinv_valid = false;
+  dev_free(g->perm, s);
+  g->perm = nullptr;
+  return IGP_OK;
 }
 
 }  // namespace igp

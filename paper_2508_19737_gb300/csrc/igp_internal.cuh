@@ -124,6 +124,9 @@ igp_status exclusive_scan(const int* in, int* out, int64_t n, int* tmp, cudaStre
 // csr_build.cu: CSR of the undirected edge list (device inputs), into g (empty).
 igp_status build_csr(const int32_t* src, const int32_t* dst, int64_t M, int32_t N, cudaStream_t s,
                      igp_graph* g);
+// csr_build.cu: merge an edge increment (device inputs) into g, growing it to N_new nodes.
+igp_status append_csr(igp_graph* g, const int32_t* src, const int32_t* dst, int64_t M, int32_t N_new,
+                      cudaStream_t s);
 // ffp.cu: batches
 igp_status batch_create(igp_graph* const* graphs, int32_t G, cudaStream_t s, igp_batch* b);
 igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uint64_t* seeds, float* out_dev,
