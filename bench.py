@@ -42,7 +42,8 @@ def parse():
     p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="dcsbm-2m", choices=sorted(synth.WORKLOADS) + sorted(synth.BATCH_WORKLOADS))
+    p.add_argument("--workload", default="dcsbm-2m", choices=sorted(synth.WORKLOADS) + sorted(synth.BATCH_WORKLOADS) + sorted(synth.SERVE_WORKLOADS))
+    p.add_argument("--slots", type=int, default=4, help="concurrent requests of the served stream")
     p.add_argument("--d", type=int, default=None, help="override the workload's embedding width")
     p.add_argument("--storage", default=None, choices=[None, "f32", "bf16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -190,6 +191,9 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    if args.workload not in synth.WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the single-graph workloads"}))
+        return 0
     wl = synth.WORKLOADS[args.workload]
     g = synth.workload_graph(args.workload)
     budget = max(0.2, min(10.0, 90.0 / max(1, args.steps + args.warmup)))
@@ -306,6 +310,143 @@ def run_batch(args):
     return 0
 
 
+def _serve_graph(args):
+    return synth.serve_graph(*args)
+
+
+def run_serve(args):
+    """The served stream: snapshot requests (an edge increment of one graph, then the FFP of
+    the whole graph so far) arriving as a Poisson process, handled by igp_server (concurrent
+    slots, admission by free device memory, resident graphs). Reported: latency p50/p99 per
+    snapshot and per graph under the stream's arrival rate; the server's throughput with every
+    request queued at once; and the same requests handled one at a time by direct library
+    calls in fp32 storage (and in the served storage). Edges come from host memory and every
+    result is copied to host memory inside the timed regions."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    wl = synth.SERVE_WORKLOADS[args.workload]
+    params = wl["stream"]
+    storage = args.storage or wl["storage"]
+    d, tau, L = args.d or wl["d"], wl["tau"], wl["L"]
+    G, T = params["G"], params["T"]
+    # graphs are drawn in a spawn pool before the first CUDA call
+    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
+        incs = list(ex.map(_serve_graph, [(params, k) for k in range(G)]))
+    times, order = synth.serve_schedule(params)
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_19737_gb300 import api
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    R = len(order)
+    nfinal = [inc[-1][2] for inc in incs]
+    outs = [torch.empty((n, d), dtype=torch.float32, pin_memory=True) for n in nfinal]
+    # directed CSR entries after each increment (for the edge*dim*layer count): from a fresh
+    # build of each graph's cumulative edges on the device, untimed
+    nnz_after = {}
+    for k in range(G):
+        gr = None
+        for t, (s_, d_, n_) in enumerate(incs[k]):
+            if gr is None:
+                gr = api.graph_build(s_, d_, n_)
+            else:
+                gr.append(s_, d_, n_)
+            nnz_after[(k, t)] = gr.nnz
+        gr.free()
+    units = sum(nnz_after[o] for o in order) * d * L
+
+    def submit(sv, k, t, st, seed):
+        s_, d_, n_ = incs[k][t]
+        return sv.submit(s_, d_, n_, tau, L, d, seed, kind="embed" if t == 0 else "append", graph_id=k,
+                         keep=(t == 0), out=outs[k], storage=st)
+
+    slots = args.slots
+    # warm-up: a few requests of the smallest graph
+    kmin = int(np.argmin(nfinal))
+    sv = api.Server(slots=slots)
+    for _ in range(max(args.warmup, 3)):
+        sv.wait(submit(sv, kmin, 0, storage, 0))
+    sv.close()
+
+    # (1) open loop at the stream's arrival rate
+    clocks = ClockSampler(local)
+    clocks.start()
+    n0 = api.launch_count()
+    sv = api.Server(slots=slots)
+    tickets = [None] * R
+    t0 = time.perf_counter()
+    for r, (k, t) in enumerate(order):
+        wait = t0 + times[r] - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        tickets[r] = submit(sv, k, t, storage, 1000 * k + t)
+    lat = [sv.wait(tk)[1] for tk in tickets]
+    t_open = time.perf_counter() - t0
+    launches_open = api.launch_count() - n0
+    first = {}
+    last = {}
+    for r, (k, t) in enumerate(order):
+        first.setdefault(k, times[r])
+        last[k] = times[r] + lat[r]
+    per_graph = [last[k] - first[k] for k in range(G)]
+    st_open = sv.stats()
+    sv.close()
+
+    # (2) saturation: every request queued at once, same order
+    sv = api.Server(slots=slots)
+    t0 = time.perf_counter()
+    tickets = [submit(sv, k, t, storage, 1000 * k + t) for k, t in order]
+    for tk in tickets:
+        sv.wait(tk)
+    t_sat = time.perf_counter() - t0
+    sv.close()
+    clk = clocks.stop()
+
+    # (3) one request at a time, direct calls (build / append, then embed to host)
+    def serial(st):
+        gr = {}
+        t0 = time.perf_counter()
+        for k, t in order:
+            s_, d_, n_ = incs[k][t]
+            if t == 0:
+                gr[k] = api.graph_build(s_, d_, n_)
+            else:
+                gr[k].append(s_, d_, n_)
+            api.embed(gr[k], tau, L, d, 1000 * k + t, out=outs[k][:n_], storage=st)
+            if t == T - 1:
+                gr.pop(k).free()
+        return time.perf_counter() - t0
+
+    t_ser32 = serial("f32")
+    t_ser = serial(storage)
+    pct = lambda v, q: float(np.percentile(np.asarray(v), q))  # noqa: E731
+    line = {
+        "metric": "served snapshot requests/s", "value": R / t_sat, "unit": "requests/s", "n_gpus": 1,
+        "steps": R, "warmup": max(args.warmup, 3), "ms_per_step": t_sat / R * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
+        "config": {"workload": args.workload, **params, "d": d, "tau": tau, "L": L, "storage": storage,
+                   "slots": slots, "requests": R, "N_total_final": int(sum(nfinal)),
+                   "step": "one snapshot request: increment merge (or CSR build) + FFP + result to host",
+                   "l2": "per-request working sets up to the largest graph; not flushed between requests"},
+        "edge_dim_layer_per_s": units / t_sat,
+        "open_loop": {"rate_offered": params["rate"], "wall_s": t_open, "rate_achieved": R / t_open,
+                      "snapshot_latency_p50_s": pct(lat, 50), "snapshot_latency_p99_s": pct(lat, 99),
+                      "graph_latency_p50_s": pct(per_graph, 50), "graph_latency_p99_s": pct(per_graph, 99),
+                      "server_p50_s": st_open["latency_p50_s"], "server_p99_s": st_open["latency_p99_s"]},
+        "serial_fp32": {"value": R / t_ser32, "unit": "requests/s", "wall_s": t_ser32},
+        f"serial_{storage}": {"value": R / t_ser, "unit": "requests/s", "wall_s": t_ser},
+        "speedup_vs_serial_fp32": t_ser32 / t_sat,
+        "gpu_launches": int(launches_open),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -313,6 +454,8 @@ def main():
         return run_reference(args)
     if args.workload in synth.BATCH_WORKLOADS:
         return run_batch(args)
+    if args.workload in synth.SERVE_WORKLOADS:
+        return run_serve(args)
     import torch
     import torch.distributed as dist
 

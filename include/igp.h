@@ -208,6 +208,82 @@ igp_status igp_batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const
 void igp_batch_free(igp_batch* b);
 
 /*
+ * Serving. A server admits requests into `slots` concurrent slots (host worker threads, each with
+ * its own CUDA stream, so the GPU work of admitted requests overlaps) as slots and device memory
+ * free up: a request starts only if its estimated peak device memory fits the server's budget
+ * (free memory at creation minus reserve_bytes) next to the running ones and the resident graphs
+ * (a request that finds nothing running starts regardless and fails with IGP_E_NOMEM if the
+ * memory is not there). Requests are picked in submission order among those that may start. Resident graphs keep
+ * their CSR and degree state on the device between requests (streaming, Alg. 2): an
+ * IGP_REQ_APPEND request grows a resident graph by an edge increment and re-embeds it; requests
+ * on the same graph_id run in submission order. Results do not depend on what else runs.
+ */
+typedef struct igp_server igp_server;
+
+typedef struct igp_server_opts {
+  int32_t slots;          /* concurrent requests, 1..64; 4 */
+  int32_t max_queue;      /* queued requests allowed (0: no limit); 0 */
+  int64_t reserve_bytes;  /* device memory left free; 1 GiB */
+  int32_t device;         /* CUDA device (-1: the current one); -1 */
+  int32_t reserved0;
+} igp_server_opts;
+
+#define IGP_REQ_EMBED  0  /* build a graph from the edges (N nodes) and embed it */
+#define IGP_REQ_APPEND 1  /* append the edges to resident graph graph_id (grown to N nodes) and embed it */
+
+/* request states reported by igp_poll / igp_wait */
+#define IGP_REQ_QUEUED    0
+#define IGP_REQ_RUNNING   1
+#define IGP_REQ_DONE      2
+#define IGP_REQ_FAILED    3
+#define IGP_REQ_CANCELLED 4
+
+typedef struct igp_request {
+  int32_t kind;         /* IGP_REQ_EMBED or IGP_REQ_APPEND */
+  int32_t keep;         /* EMBED: keep the built graph resident under graph_id */
+  int64_t graph_id;     /* caller-chosen id of a resident graph */
+  const int32_t* src;   /* HOST edge arrays, M entries each; copied by igp_submit */
+  const int32_t* dst;
+  int64_t M;
+  int32_t N;            /* nodes after this request */
+  int32_t L;            /* layers */
+  double tau;
+  int32_t d;
+  int32_t reserved0;
+  uint64_t seed;
+  igp_embed_opts opts;  /* as for igp_embed; x_in and profile must be NULL */
+  float* out;           /* HOST N x d fp32, written when the request is done; keep it valid until then */
+} igp_request;
+
+typedef struct igp_server_stats {
+  int64_t submitted, completed, failed, cancelled, queued, running, resident_graphs;
+  int64_t admitted_bytes;  /* estimated peak device bytes of the running requests */
+  int64_t budget_bytes;    /* free device memory at igp_server_create minus reserve_bytes */
+  double latency_p50_s, latency_p99_s;  /* submit-to-done latency of completed requests */
+  int64_t resident_bytes;  /* device bytes held by resident graphs */
+} igp_server_stats;
+
+/* Defaults as listed in igp_server_opts. */
+void igp_server_opts_init(igp_server_opts* opts);
+/* Start a server (its worker threads). Errors: IGP_E_INVAL, IGP_E_CUDA. */
+igp_status igp_server_create(const igp_server_opts* opts, igp_server** out);
+/* Cancel queued requests, wait for running ones, free resident graphs and the server. */
+void igp_server_destroy(igp_server* sv);
+/* Queue a request; *ticket identifies it. Errors: IGP_E_INVAL (bad request), IGP_E_BUSY (queue full
+ * or stopping), IGP_E_NOMEM (the request alone exceeds the memory budget). Non-blocking. */
+igp_status igp_submit(igp_server* sv, const igp_request* r, uint64_t* ticket);
+/* Non-blocking state of a request: IGP_OK when done, IGP_E_NOTREADY while queued or running, the
+ * request's own error when it failed, IGP_E_CANCELLED; *latency_s = submit-to-done time. */
+igp_status igp_poll(igp_server* sv, uint64_t ticket, int32_t* state, double* latency_s);
+/* Like igp_poll after waiting up to timeout_s seconds (< 0: no limit) for the request to finish. */
+igp_status igp_wait(igp_server* sv, uint64_t ticket, double timeout_s, int32_t* state, double* latency_s);
+/* Cancel a queued request (IGP_E_BUSY once it runs). */
+igp_status igp_cancel(igp_server* sv, uint64_t ticket);
+/* Free a resident graph (waits for a request running on it). */
+igp_status igp_server_release(igp_server* sv, int64_t graph_id);
+igp_status igp_server_get_stats(igp_server* sv, igp_server_stats* stats);
+
+/*
  * igp_embed without any memory allocation. (The paper has no counterpart: this serves callers that
  * may not allocate device memory at the moment they call, e.g. code recording a CUDA stream capture,
  * where cudaMalloc is not allowed, an allocator or memory-manager hook that must not re-enter the

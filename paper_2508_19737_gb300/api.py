@@ -66,6 +66,30 @@ class EmbedOpts(ctypes.Structure):
     ]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_queue", ctypes.c_int32), ("reserve_bytes", ctypes.c_int64),
+                ("device", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("keep", ctypes.c_int32), ("graph_id", ctypes.c_int64),
+                ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("M", ctypes.c_int64), ("N", ctypes.c_int32),
+                ("L", ctypes.c_int32), ("tau", ctypes.c_double), ("d", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("seed", ctypes.c_uint64), ("opts", EmbedOpts),
+                ("out", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "cancelled", "queued", "running",
+                                              "resident_graphs", "admitted_bytes", "budget_bytes")] + \
+               [("latency_p50_s", ctypes.c_double), ("latency_p99_s", ctypes.c_double),
+                ("resident_bytes", ctypes.c_int64)]
+
+
+IGP_REQ_EMBED = 0
+IGP_REQ_APPEND = 1
+REQ_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled"}
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -103,6 +127,17 @@ _SIGS = {
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(EmbedOpts),
                                          ctypes.c_void_p]),
     "igp_batch_free": (None, [ctypes.c_void_p]),
+    "igp_server_opts_init": (None, [ctypes.POINTER(ServerOpts)]),
+    "igp_server_create": (ctypes.c_int32, [ctypes.POINTER(ServerOpts), ctypes.POINTER(ctypes.c_void_p)]),
+    "igp_server_destroy": (None, [ctypes.c_void_p]),
+    "igp_submit": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "igp_poll": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_double)]),
+    "igp_wait": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_double)]),
+    "igp_cancel": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64]),
+    "igp_server_release": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64]),
+    "igp_server_get_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
     "igp_profile_create": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_void_p)]),
     "igp_profile_free": (None, [ctypes.c_void_p]),
     "igp_profile_read": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
@@ -365,5 +400,78 @@ class Batch:
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owning wrapper of an igp_server: queued, memory-admitted, concurrent embed / append requests."""
+
+    def __init__(self, slots=4, max_queue=0, reserve_bytes=1 << 30, device=-1):
+        o = ServerOpts()
+        lib().igp_server_opts_init(ctypes.byref(o))
+        o.slots, o.max_queue, o.reserve_bytes, o.device = slots, max_queue, reserve_bytes, device
+        h = ctypes.c_void_p()
+        _check(lib().igp_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h.value
+        self._outs = {}
+
+    def submit(self, src, dst, N, tau, L, d, seed, kind="embed", graph_id=0, keep=False, out=None, **kw):
+        """Queue a request (host int32 edge arrays, copied now); returns its ticket. The result lands in
+        `out` (a new float32 N x d array unless given), available from result() once done."""
+        src = np.ascontiguousarray(src, dtype=np.int32)
+        dst = np.ascontiguousarray(dst, dtype=np.int32)
+        if out is None:
+            out = np.empty((N, d), dtype=np.float32)
+        r = Request()
+        r.kind = IGP_REQ_EMBED if kind == "embed" else IGP_REQ_APPEND
+        r.keep = 1 if keep else 0
+        r.graph_id = int(graph_id)
+        r.src, r.dst, r.M, r.N = src.ctypes.data, dst.ctypes.data, src.size, int(N)
+        r.tau, r.L, r.d, r.seed = float(tau), int(L), int(d), int(seed) & 0xFFFFFFFFFFFFFFFF
+        r.opts = embed_opts(**kw)
+        r.out = _ptr(out)
+        t = ctypes.c_uint64()
+        _check(lib().igp_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
+        self._outs[t.value] = out
+        return t.value
+
+    def poll(self, ticket):
+        st = ctypes.c_int32()
+        lat = ctypes.c_double()
+        code = lib().igp_poll(self.handle, ticket, ctypes.byref(st), ctypes.byref(lat))
+        return REQ_STATES[st.value], lat.value, code
+
+    def wait(self, ticket, timeout=-1.0):
+        """Wait for a request; returns (state, latency_s); raises IgpError if it failed."""
+        st = ctypes.c_int32()
+        lat = ctypes.c_double()
+        code = lib().igp_wait(self.handle, ticket, float(timeout), ctypes.byref(st), ctypes.byref(lat))
+        if code not in (IGP_OK, IGP_E_NOTREADY, IGP_E_CANCELLED):
+            raise IgpError(code, lib().igp_last_error().decode())
+        return REQ_STATES[st.value], lat.value
+
+    def result(self, ticket):
+        return self._outs[ticket]
+
+    def cancel(self, ticket):
+        _check(lib().igp_cancel(self.handle, ticket))
+
+    def release(self, graph_id):
+        _check(lib().igp_server_release(self.handle, int(graph_id)))
+
+    def stats(self):
+        s = ServerStats()
+        _check(lib().igp_server_get_stats(self.handle, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.handle:
+            lib().igp_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass

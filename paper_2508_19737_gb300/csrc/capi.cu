@@ -94,7 +94,7 @@ bool is_device_ptr(const void* p) {
 }
 
 int num_sms() {
-  static int sms[64] = {};
+  static std::atomic<int> sms[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;

@@ -1322,7 +1322,7 @@ __global__ void k_output_batch(const S* __restrict__ T, const float* __restrict_
 template <int D, typename S>
 struct LayerCfg {
   static int per_sm() {
-    static int v = 0;
+    static std::atomic<int> v{0};  // filled once; concurrent server threads may race to fill it
     if (v == 0) {
       int b = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_layer<D, S>, kLayerThreads, 0);
@@ -1354,7 +1354,7 @@ constexpr size_t kTmaDynSmem = (size_t)kLayerWarps * kTmaStages * (kTmaStageByte
 template <int D, typename S>
 struct TmaCfg {
   static int per_sm() {
-    static int v = 0;
+    static std::atomic<int> v{0};  // filled once; concurrent server threads may race to fill it
     if (v == 0) {
       cudaFuncSetAttribute(k_layer_tma<D, S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaDynSmem);
       int b = 0;
@@ -1462,7 +1462,7 @@ igp_status prescale_launch(const void* x, const float* dinv, int32_t N, int32_t 
 template <int D, typename S>
 struct BatchCfg {
   static int per_sm() {
-    static int v = 0;
+    static std::atomic<int> v{0};  // filled once; concurrent server threads may race to fill it
     if (v == 0) {
       int b = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_layer_batch<D, S>, kLayerThreads, 0);

@@ -1,0 +1,414 @@
+// Serving loop (igp_server_*): requests to embed graphs, or to grow a resident graph by an
+// edge increment and re-embed it (Alg. 2, lines 1-7), are queued, admitted into a fixed
+// number of slots as device memory and slots free up, and run concurrently: every slot
+// is a host worker thread with its own CUDA stream, so the GPU work of admitted requests
+// overlaps. Resident graphs keep their CSR and degree state on the device between
+// requests; requests on the same resident graph run in submission order.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <set>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "igp_internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+  uint64_t ticket = 0;
+  igp_request r;  // pointers of the caller: src/dst replaced by the copies below
+  std::vector<int32_t> src, dst;
+  int32_t state = IGP_REQ_QUEUED;
+  igp_status status = IGP_OK;
+  std::string error;
+  size_t est = 0;
+  Clock::time_point t_submit, t_start, t_done;
+};
+
+}  // namespace
+
+struct igp_server {
+  igp_server_opts opts;
+  int device = 0;
+  size_t budget = 0, admitted = 0;  // device bytes: usable, held by running requests
+  size_t resident_bytes = 0;         // device bytes held by resident graphs
+  std::map<int64_t, size_t> resident_size;
+  std::mutex mu;
+  std::condition_variable cv;       // work or completion
+  std::deque<Req*> queue;
+  std::map<uint64_t, Req*> reqs;
+  std::map<int64_t, igp_graph*> resident;
+  std::set<int64_t> busy;           // resident graph ids with a running request
+  std::vector<std::thread> workers;
+  std::vector<double> latencies;
+  uint64_t next_ticket = 1;
+  int64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, running = 0;
+  bool stopping = false;
+};
+
+namespace {
+
+// Device bytes a request may hold at its peak (edge copies, CSR build temporaries, the
+// CSR, per-node arrays, the two activation buffers and the output staging).
+size_t estimate(const igp_server* sv, const igp_request& r) {
+  const size_t sb = r.opts.storage == IGP_STORE_BF16 ? 2 : 4;
+  size_t n = (size_t)r.N, m = (size_t)r.M;
+  size_t bytes = 40 * m + 48 * n + n * (size_t)r.d * (2 * sb + 4) + (1u << 20);
+  if (r.kind == IGP_REQ_APPEND) {
+    auto it = sv->resident.find(r.graph_id);
+    if (it != sv->resident.end()) bytes += 12 * (size_t)it->second->nnz;
+  }
+  return bytes;
+}
+
+// Device bytes a graph handle holds between calls (CSR, Eq. 1 factors, order, workspace).
+size_t graph_bytes(const igp_graph* g) {
+  return 4 * ((size_t)g->N + 1) + 4 * (size_t)g->nnz + 12 * (size_t)g->N + g->ws_bytes;
+}
+
+void set_resident(igp_server* sv, int64_t id, igp_graph* g) {
+  auto it = sv->resident_size.find(id);
+  if (it != sv->resident_size.end()) sv->resident_bytes -= it->second;
+  if (g) {
+    const size_t b = graph_bytes(g);
+    sv->resident_size[id] = b;
+    sv->resident_bytes += b;
+  } else if (it != sv->resident_size.end()) {
+    sv->resident_size.erase(it);
+  }
+}
+
+// First queued request that may start now: memory fits, and no earlier request on the
+// same resident graph is queued or running.
+Req* pick(igp_server* sv) {
+  std::set<int64_t> seen;
+  for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
+    Req* q = *it;
+    const bool on_graph = q->r.kind == IGP_REQ_APPEND || q->r.keep;
+    if (on_graph) {
+      if (seen.count(q->r.graph_id) || sv->busy.count(q->r.graph_id)) {
+        seen.insert(q->r.graph_id);
+        continue;
+      }
+      seen.insert(q->r.graph_id);
+    }
+    if (q->r.kind == IGP_REQ_APPEND && !sv->resident.count(q->r.graph_id)) {
+      // nothing earlier will create this graph: the request fails without running
+      q->est = 0;
+      q->status = IGP_E_INVAL;
+      q->error = "igp_submit: no resident graph with this graph_id";
+      sv->queue.erase(it);
+      return q;
+    }
+    q->est = estimate(sv, q->r);
+    if (sv->admitted + sv->resident_bytes + q->est > sv->budget && sv->running > 0) continue;  // wait for memory
+    sv->queue.erase(it);
+    return q;
+  }
+  return nullptr;
+}
+
+void run(igp_server* sv, Req* q, cudaStream_t s) {
+  igp_request& r = q->r;
+  igp_graph* g = nullptr;
+  igp_status st = IGP_OK;
+  if (r.kind == IGP_REQ_EMBED) {
+    st = igp_graph_build(q->src.data(), q->dst.data(), r.M, r.N, s, &g);
+  } else {
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      g = sv->resident[r.graph_id];
+    }
+    st = igp_graph_append(g, q->src.data(), q->dst.data(), r.M, r.N, s);
+  }
+  if (st == IGP_OK) st = igp_embed(g, r.tau, r.L, r.d, r.seed, r.out, &r.opts, s);
+  if (st != IGP_OK) q->error = igp_last_error();
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (r.kind == IGP_REQ_EMBED) {
+    if (st == IGP_OK && r.keep) {
+      auto it = sv->resident.find(r.graph_id);
+      if (it != sv->resident.end()) igp_graph_free(it->second);
+      sv->resident[r.graph_id] = g;
+      set_resident(sv, r.graph_id, g);
+    } else if (g) {
+      igp_graph_free(g);
+    }
+  } else {
+    set_resident(sv, r.graph_id, g);  // grown by the increment (unchanged if the merge failed)
+  }
+  q->status = st;
+}
+
+void worker(igp_server* sv) {
+  cudaSetDevice(sv->device);
+  cudaStream_t s = nullptr;
+  cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  for (;;) {
+    Req* q = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      for (;;) {
+        if (sv->stopping && sv->queue.empty()) break;
+        q = pick(sv);
+        if (q || sv->stopping) break;
+        sv->cv.wait(lk);
+      }
+      if (!q) break;
+      q->state = IGP_REQ_RUNNING;
+      q->t_start = Clock::now();
+      sv->admitted += q->est;
+      sv->running += 1;
+      if (q->r.kind == IGP_REQ_APPEND || q->r.keep) sv->busy.insert(q->r.graph_id);
+    }
+    if (q->status == IGP_OK) run(sv, q, s);
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      q->t_done = Clock::now();
+      q->state = q->status == IGP_OK ? IGP_REQ_DONE : IGP_REQ_FAILED;
+      sv->admitted -= q->est;
+      sv->running -= 1;
+      if (q->r.kind == IGP_REQ_APPEND || q->r.keep) sv->busy.erase(q->r.graph_id);
+      if (q->status == IGP_OK) {
+        sv->completed += 1;
+        sv->latencies.push_back(std::chrono::duration<double>(q->t_done - q->t_submit).count());
+      } else {
+        sv->failed += 1;
+      }
+      q->src.clear();
+      q->src.shrink_to_fit();
+      q->dst.clear();
+      q->dst.shrink_to_fit();
+    }
+    sv->cv.notify_all();
+  }
+  cudaStreamDestroy(s);
+}
+
+double pct(std::vector<double> v, double p) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  const size_t k = (size_t)std::min<double>((double)v.size() - 1, p * (double)(v.size() - 1) + 0.5);
+  return v[k];
+}
+
+}  // namespace
+
+using namespace igp;
+
+extern "C" {
+
+void igp_server_opts_init(igp_server_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->slots = 4;
+  o->max_queue = 0;
+  o->reserve_bytes = 1ll << 30;
+  o->device = -1;
+}
+
+igp_status igp_server_create(const igp_server_opts* opts, igp_server** out) {
+  clear_error();
+  if (!out) return IGP_E_INVAL;
+  *out = nullptr;
+  igp_server_opts o;
+  if (opts)
+    o = *opts;
+  else
+    igp_server_opts_init(&o);
+  if (o.slots < 1 || o.slots > 64 || o.max_queue < 0 || o.reserve_bytes < 0) {
+    set_error("igp_server_create: need 1 <= slots <= 64, max_queue >= 0, reserve_bytes >= 0");
+    return IGP_E_INVAL;
+  }
+  igp_server* sv = new (std::nothrow) igp_server();
+  if (!sv) return IGP_E_NOMEM;
+  sv->opts = o;
+  if (o.device >= 0) {
+    cudaError_t e = cudaSetDevice(o.device);
+    if (e != cudaSuccess) {
+      delete sv;
+      return cuda_status(e, "cudaSetDevice", __FILE__, __LINE__);
+    }
+  }
+  cudaGetDevice(&sv->device);
+  size_t fr = 0, tot = 0;
+  cudaError_t e = cudaMemGetInfo(&fr, &tot);
+  if (e != cudaSuccess) {
+    delete sv;
+    return cuda_status(e, "cudaMemGetInfo", __FILE__, __LINE__);
+  }
+  sv->budget = fr > (size_t)o.reserve_bytes ? fr - (size_t)o.reserve_bytes : 0;
+  for (int k = 0; k < o.slots; ++k) sv->workers.emplace_back(worker, sv);
+  *out = sv;
+  return IGP_OK;
+}
+
+void igp_server_destroy(igp_server* sv) {
+  if (!sv) return;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (Req* q : sv->queue) {
+      q->state = IGP_REQ_CANCELLED;
+      sv->cancelled += 1;
+    }
+    sv->queue.clear();
+    sv->stopping = true;
+  }
+  sv->cv.notify_all();
+  for (auto& t : sv->workers) t.join();
+  for (auto& kv : sv->resident) igp_graph_free(kv.second);
+  for (auto& kv : sv->reqs) delete kv.second;
+  delete sv;
+}
+
+igp_status igp_submit(igp_server* sv, const igp_request* r, uint64_t* ticket) {
+  clear_error();
+  if (!sv || !r || !ticket || !r->out || r->N < 1 || r->M < 0 || (r->M > 0 && (!r->src || !r->dst)) ||
+      (r->kind != IGP_REQ_EMBED && r->kind != IGP_REQ_APPEND) || r->opts.x_in || r->opts.profile) {
+    set_error("igp_submit: invalid request (kind, N, M, edges, out; opts.x_in and opts.profile must be NULL)");
+    return IGP_E_INVAL;
+  }
+  Req* q = new (std::nothrow) Req();
+  if (!q) return IGP_E_NOMEM;
+  q->r = *r;
+  q->src.assign(r->src, r->src + r->M);
+  q->dst.assign(r->dst, r->dst + r->M);
+  q->r.src = nullptr;
+  q->r.dst = nullptr;
+  q->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stopping || (sv->opts.max_queue > 0 && (int)sv->queue.size() >= sv->opts.max_queue)) {
+      delete q;
+      set_error("igp_submit: the server is stopping or its queue is full");
+      return IGP_E_BUSY;
+    }
+    const size_t est = estimate(sv, q->r);
+    if (est > sv->budget) {
+      delete q;
+      set_error("igp_submit: the request needs about %zu device bytes, more than the server's %zu", est,
+                sv->budget);
+      return IGP_E_NOMEM;
+    }
+    q->ticket = sv->next_ticket++;
+    sv->reqs[q->ticket] = q;
+    sv->queue.push_back(q);
+    sv->submitted += 1;
+    *ticket = q->ticket;
+  }
+  sv->cv.notify_all();
+  return IGP_OK;
+}
+
+static igp_status report(Req* q, int32_t* state, double* latency_s) {
+  if (state) *state = q->state;
+  if (latency_s)
+    *latency_s = q->state == IGP_REQ_DONE || q->state == IGP_REQ_FAILED
+                     ? std::chrono::duration<double>(q->t_done - q->t_submit).count()
+                     : 0.0;
+  if (q->state == IGP_REQ_FAILED) {
+    set_error("%s", q->error.c_str());
+    return q->status;
+  }
+  if (q->state == IGP_REQ_CANCELLED) return IGP_E_CANCELLED;
+  return (q->state == IGP_REQ_DONE) ? IGP_OK : IGP_E_NOTREADY;
+}
+
+igp_status igp_poll(igp_server* sv, uint64_t ticket, int32_t* state, double* latency_s) {
+  clear_error();
+  if (!sv) return IGP_E_INVAL;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) {
+    set_error("igp_poll: unknown ticket %llu", (unsigned long long)ticket);
+    return IGP_E_INVAL;
+  }
+  return report(it->second, state, latency_s);
+}
+
+igp_status igp_wait(igp_server* sv, uint64_t ticket, double timeout_s, int32_t* state, double* latency_s) {
+  clear_error();
+  if (!sv) return IGP_E_INVAL;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) {
+    set_error("igp_wait: unknown ticket %llu", (unsigned long long)ticket);
+    return IGP_E_INVAL;
+  }
+  Req* q = it->second;
+  auto finished = [&] { return q->state >= IGP_REQ_DONE; };
+  if (timeout_s < 0)
+    sv->cv.wait(lk, finished);
+  else
+    sv->cv.wait_for(lk, std::chrono::duration<double>(timeout_s), finished);
+  return report(q, state, latency_s);
+}
+
+igp_status igp_cancel(igp_server* sv, uint64_t ticket) {
+  clear_error();
+  if (!sv) return IGP_E_INVAL;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) {
+      set_error("igp_cancel: unknown ticket %llu", (unsigned long long)ticket);
+      return IGP_E_INVAL;
+    }
+    Req* q = it->second;
+    if (q->state != IGP_REQ_QUEUED) {
+      set_error("igp_cancel: the request is no longer queued");
+      return IGP_E_BUSY;
+    }
+    sv->queue.erase(std::find(sv->queue.begin(), sv->queue.end(), q));
+    q->state = IGP_REQ_CANCELLED;
+    sv->cancelled += 1;
+  }
+  sv->cv.notify_all();
+  return IGP_OK;
+}
+
+igp_status igp_server_release(igp_server* sv, int64_t graph_id) {
+  clear_error();
+  if (!sv) return IGP_E_INVAL;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  sv->cv.wait(lk, [&] { return !sv->busy.count(graph_id); });
+  auto it = sv->resident.find(graph_id);
+  if (it == sv->resident.end()) {
+    set_error("igp_server_release: no resident graph %lld", (long long)graph_id);
+    return IGP_E_INVAL;
+  }
+  igp_graph_free(it->second);
+  sv->resident.erase(it);
+  set_resident(sv, graph_id, nullptr);
+  return IGP_OK;
+}
+
+igp_status igp_server_get_stats(igp_server* sv, igp_server_stats* st) {
+  clear_error();
+  if (!sv || !st) return IGP_E_INVAL;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  memset(st, 0, sizeof(*st));
+  st->submitted = sv->submitted;
+  st->completed = sv->completed;
+  st->failed = sv->failed;
+  st->cancelled = sv->cancelled;
+  st->queued = (int64_t)sv->queue.size();
+  st->running = sv->running;
+  st->resident_graphs = (int64_t)sv->resident.size();
+  st->admitted_bytes = (int64_t)sv->admitted;
+  st->budget_bytes = (int64_t)sv->budget;
+  st->resident_bytes = (int64_t)sv->resident_bytes;
+  st->latency_p50_s = pct(sv->latencies, 0.50);
+  st->latency_p99_s = pct(sv->latencies, 0.99);
+  return IGP_OK;
+}
+
+}  // extern "C"

@@ -183,39 +183,30 @@ def split_increments(graph, T=10, mode="random", seed=0):
                 for a, b in zip(cuts[:-1], cuts[1:])]
     if mode != "snowball":
         raise ValueError(mode)
-    # adjacency lists for BFS
+    # breadth-first visit order; a component not reached from the start is entered at its
+    # first node in a random node order once everything reachable has been visited
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import breadth_first_order, connected_components
     keep = src != dst
-    u = np.concatenate([src[keep], dst[keep]])
-    v = np.concatenate([dst[keep], src[keep]])
-    o = np.argsort(u, kind="stable")
-    u, v = u[o], v[o]
-    ptr = np.searchsorted(u, np.arange(N + 1))
-    visit = np.full(N, -1, dtype=np.int64)
-    order = []
+    adj = sp.csr_matrix((np.ones(int(keep.sum()), dtype=np.int8), (src[keep], dst[keep])), shape=(N, N))
+    ncomp, comp = connected_components(adj, directed=False)
+    sizes = np.bincount(comp, minlength=ncomp)
     start = int(rng.integers(N))
     rest = rng.permutation(N)
-    ri = 0
-    frontier = [start]
-    visit[start] = 0
-    order.append(start)
-    while len(order) < N:
-        nxt = []
-        for a in frontier:
-            for b in v[ptr[a]:ptr[a + 1]]:
-                if visit[b] < 0:
-                    visit[b] = len(order)
-                    order.append(int(b))
-                    nxt.append(int(b))
-        if not nxt:
-            while ri < N and visit[rest[ri]] >= 0:
-                ri += 1
-            if ri >= N:
-                break
-            b = int(rest[ri])
-            visit[b] = len(order)
-            order.append(b)
-            nxt = [b]
-        frontier = nxt
+    entries = [start]
+    seen = np.zeros(ncomp, dtype=bool)
+    seen[comp[start]] = True
+    for b_ in rest[np.sort(np.unique(comp[rest], return_index=True)[1])]:  # each component's first node
+        if not seen[comp[b_]]:
+            seen[comp[b_]] = True
+            entries.append(int(b_))
+    parts = []
+    for e in entries:
+        parts.append(np.array([e]) if sizes[comp[e]] == 1 else
+                     breadth_first_order(adj, e, directed=False, return_predecessors=False))
+    order = np.concatenate(parts).astype(np.int64)
+    visit = np.empty(N, dtype=np.int64)
+    visit[order] = np.arange(N)
     pos = visit  # relabel: node -> visit position
     su, sv = pos[src], pos[dst]
     later = np.maximum(su, sv)
@@ -263,3 +254,46 @@ def workload_graph(name):
 def workload_batch(name):
     b = BATCH_WORKLOADS[name]["batch"]
     return batch_dcsbm(b["G"], b["n_lo"], b["n_hi"], b["deg_lo"], b["deg_hi"], b["gamma"], b["ratio"], seed=b["seed"])
+
+
+# A served stream: G graphs, N log-uniform on [5,000, 1,000,000], blocks round(N^0.4), mean
+# degree 25, gamma 2.5, ratio 5; each graph arrives as T = 10 equal edge increments (even
+# graphs in uniformly random edge order, odd graphs in snowball order); requests arrive as a
+# Poisson process of the given rate, each the next increment of a uniformly chosen graph
+# that still has increments left.
+SERVE_WORKLOADS = {
+    "dcsbm-serve": dict(stream=dict(G=32, n_lo=5000, n_hi=1_000_000, mean_deg=25, gamma=2.5, ratio=5, T=10,
+                                    rate=200.0, seed=0),
+                        d=64, tau=-0.5, L=10, storage="bf16"),
+}
+
+
+def serve_graph(params, k):
+    """Increments of graph k of a served stream: list of (src, dst, N_t)."""
+    ss = np.random.SeedSequence(params["seed"])
+    rng = np.random.default_rng(ss)
+    Ns = log_uniform_sizes(rng, params["G"], params["n_lo"], params["n_hi"])
+    kid = ss.spawn(params["G"])[k]
+    N = int(Ns[k])
+    g = dcsbm(N, max(1, int(round(N ** 0.4))), params["mean_deg"], params["gamma"], params["ratio"], seed=kid)
+    mode = "random" if k % 2 == 0 else "snowball"
+    return split_increments(g, params["T"], mode, seed=int(kid.generate_state(1)[0]))
+
+
+def serve_schedule(params):
+    """Arrival times (s, from 0) and the (graph, increment) each request carries."""
+    rng = np.random.default_rng(np.random.SeedSequence([params["seed"], 1]))
+    G, T = params["G"], params["T"]
+    R = G * T
+    times = np.cumsum(rng.exponential(1.0 / params["rate"], size=R))
+    times -= times[0]
+    left = [T] * G
+    live = list(range(G))
+    order = []
+    for _ in range(R):
+        k = live[int(rng.integers(len(live)))]
+        order.append((k, T - left[k]))
+        left[k] -= 1
+        if left[k] == 0:
+            live.remove(k)
+    return times, order
