@@ -304,6 +304,16 @@ constexpr int kChunk = 8;  // neighbour rows in flight per row group per trip
 #ifndef IGP_LAYER_MIN_CTAS
 #define IGP_LAYER_MIN_CTAS 2  // resident CTAs per SM the register budget is sized for
 #endif
+// L2 prefetch distance of the neighbour rows, in trips (0: no prefetch). The row loads of a
+// trip then find their lines in L2 instead of waiting on DRAM.
+#ifndef IGP_LAYER_PF
+#define IGP_LAYER_PF 2
+#endif
+
+// Fetch the 128-byte line holding p into L2 (no data returned to the SM).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 
 // tanh of Eq. 4. With fp32 storage: CUDA's tanhf. With bf16 storage the result is
@@ -450,6 +460,26 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
     }
   };
 
+  // L2 prefetch of neighbour rows: lane lig takes the trip entries it holds indices for
+  // (as load_idx) and fetches every 128-byte line of each such row into L2
+  const S* __restrict__ Tblk = Tin_all + (int64_t)blockIdx.y * N * D;
+  auto load_pf = [&](int (&p)[IPL], int base, int end) {
+#pragma unroll
+    for (int k = 0; k < IPL; ++k) {
+      const int t = lig + G * k;
+      p[k] = (t < C && base + t < end) ? __ldg(col + base + t) : -1;
+    }
+  };
+  auto prefetch_rows = [&](const int (&p)[IPL]) {
+    constexpr int kLines = (int)(D * sizeof(S)) > 128 ? (int)(D * sizeof(S)) / 128 : 1;
+#pragma unroll
+    for (int k = 0; k < IPL; ++k)
+      if (p[k] >= 0) {
+#pragma unroll
+        for (int q = 0; q < kLines; ++q) prefetch_l2(Tblk + (int64_t)p[k] * D + q * (128 / (int)sizeof(S)));
+      }
+  };
+
   // three-stage pipeline over tiles: row id (t+2), row data (t+1), gathers (t)
   int r = row_at(w0);
   RowData cur;
@@ -471,6 +501,13 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
       const int c = cur.b + tr * C;
       int jn[IPL];
       load_idx(jn, c + C, cur.e);
+#if IGP_LAYER_PF > 0
+      // prefetch targets: this tile's trip tr + PF, and the next tile's trip tr (its first
+      // PF trips; in decreasing-degree order the next tile has no more trips than this one)
+      int pa[IPL], pb[IPL];
+      load_pf(pa, c + IGP_LAYER_PF * C, cur.e);
+      load_pf(pb, nxt.b + tr * C, tr < IGP_LAYER_PF ? nxt.e : 0);
+#endif
       RT x[C];
 #pragma unroll
       for (int t = 0; t < C; ++t) {
@@ -479,6 +516,10 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
       }
 #pragma unroll
       for (int t = 0; t < C; ++t) RW::add(acc, x[t]);
+#if IGP_LAYER_PF > 0
+      prefetch_rows(pa);
+      prefetch_rows(pb);
+#endif
 #pragma unroll
       for (int k = 0; k < IPL; ++k) jw[k] = jn[k];
     }
