@@ -199,18 +199,32 @@ __global__ void k_theta(uint64_t seed, int32_t N, int32_t d, int32_t dc, float x
 }
 
 // ------------------------------------------------------------------ per-graph helpers
-// w_i = sum_{j in N(i)} dinv_j, one warp per row, fixed order.
+// w_i = sum_{j in N(i)} dinv_j, fixed order: eight lanes per row, lane s adding entries
+// s, s + 8, s + 16, .. (four index loads, then four gathers, in flight at a time), then an
+// xor tree over the eight lanes. A warp takes four consecutive rows per tile.
 __global__ void k_wsum(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                        const float* __restrict__ dinv, int32_t N, float* __restrict__ wsum) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < N;
-       i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const int b = row_ptr[i], e = row_ptr[i + 1];
+  const int sub = threadIdx.x & 7, grp = (threadIdx.x & 31) >> 3;
+  const int64_t ntiles = ((int64_t)N + 3) >> 2;
+  for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < ntiles;
+       tile += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t i = tile * 4 + grp;
+    const bool ok = i < N;
+    const int b = ok ? row_ptr[i] : 0, e = ok ? row_ptr[i + 1] : 0;
     float a = 0.0f;
-    for (int k = b + lane; k < e; k += 32) a += __ldg(dinv + __ldg(col + k));
+    for (int k0 = b + sub; k0 < e; k0 += 32) {
+      int j[4];
 #pragma unroll
-    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) wsum[i] = a;
+      for (int q = 0; q < 4; ++q) j[q] = k0 + 8 * q < e ? __ldg(col + k0 + 8 * q) : -1;
+      float w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) w[q] = j[q] >= 0 ? __ldg(dinv + j[q]) : 0.0f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) a += w[q];
+    }
+#pragma unroll
+    for (int o = 4; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (ok && sub == 0) wsum[i] = a;
   }
 }
 
@@ -298,7 +312,10 @@ __global__ void k_prescale(const S* __restrict__ x, const float* __restrict__ di
 }
 
 // ------------------------------------------------------------------ Eq. 4 layer
-constexpr int kChunk = 8;  // neighbour rows in flight per row group per trip
+#ifndef IGP_LAYER_CHUNK
+#define IGP_LAYER_CHUNK 8
+#endif
+constexpr int kChunk = IGP_LAYER_CHUNK;  // neighbour rows in flight per row group per trip
 
 // Build-time tuning of the register-load layer kernel (defaults are the measured best).
 #ifndef IGP_LAYER_MIN_CTAS
@@ -400,6 +417,7 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
   constexpr int C = kChunk;                // neighbour rows per trip
   constexpr int IPL = C >= G ? C / G : 1;  // trip indices held per lane
   static_assert(G >= 1 && G <= 32 && GPW * G == 32, "unsupported width");
+  static_assert(C <= G || C % G == 0, "kChunk must be at most, or a multiple of, the lanes per row");
 
   __shared__ float s_mu[D], s_is[D];
   __shared__ long long s_red[kLayerWarps][2 * D];
@@ -1632,7 +1650,7 @@ igp_status launch_dinv_wsum(const int32_t* row_ptr, const int32_t* col, int32_t 
   int blocks = (int)std::min<int64_t>(((int64_t)N + 255) / 256, (int64_t)num_sms() * 8);
   k_dinv<<<std::max(blocks, 1), 256, 0, s>>>(row_ptr, N, tau, eps, dinv);
   IGP_TRY(after_launch("k_dinv"));
-  int wblocks = (int)std::min<int64_t>(((int64_t)N * 32 + 255) / 256, (int64_t)num_sms() * 16);
+  int wblocks = (int)std::min<int64_t>(((int64_t)N * 8 + 255) / 256, (int64_t)num_sms() * 8);
   k_wsum<<<std::max(wblocks, 1), 256, 0, s>>>(row_ptr, col, dinv, N, wsum);
   return after_launch("k_wsum");
 }

@@ -60,6 +60,10 @@ CSR_CASES = {
         np.concatenate([np.random.default_rng(2).integers(1, 70000, 60000).astype(np.int32),
                         np.random.default_rng(3).integers(0, 70000, 3000).astype(np.int32),
                         np.arange(2, 5001, dtype=np.int32)]), 70000),
+    # 2^22 nodes: the partitioned build packs (local row, column) into all 32 bits
+    "wide-ids": lambda: (*_random_multigraph(4, 1 << 22, 30000), 1 << 22),
+    # more than 2^24 nodes: the atomic build
+    "huge-N": lambda: (*_random_multigraph(5, (1 << 24) + 5, 30000), (1 << 24) + 5),
 }
 
 
