@@ -19,9 +19,12 @@
 //     values), so a neighbour row is G coalesced 16-byte loads;
 //   * rows are visited in decreasing-degree order (perm) in warp tiles of 32/G rows, so
 //     the groups of a warp have (nearly) the same trip count and stay converged;
-//   * kChunk neighbour rows per group are in flight per trip; the next trip's column
+//   * kChunk (16) neighbour rows per group are in flight per trip; the next trip's column
 //     indices and the next tiles' rows (perm entry two tiles ahead, row bounds, self
-//     row, dinv, w one tile ahead) are prefetched during the current trip;
+//     row, dinv, w one tile ahead) are loaded during the current trip;
+//   * when the gathered slice of T^(l-1) is larger than L2 can hold, each trip also
+//     issues prefetch.global.L2 for the rows of the trip after next (and of the next
+//     tile's first trip), so that the register loads find their lines in L2;
 //   * column indices are loaded evict-first (streamed once); outputs stored streaming;
 //     bf16 neighbour rows are added with mixed-precision adds (one instruction a value);
 //   * wide rows can be split into column chunks (blockIdx.y) over a column-blocked
@@ -313,19 +316,25 @@ __global__ void k_prescale(const S* __restrict__ x, const float* __restrict__ di
 
 // ------------------------------------------------------------------ Eq. 4 layer
 #ifndef IGP_LAYER_CHUNK
-#define IGP_LAYER_CHUNK 8
+#define IGP_LAYER_CHUNK 16
 #endif
 constexpr int kChunk = IGP_LAYER_CHUNK;  // neighbour rows in flight per row group per trip
+constexpr int kTmaChunk = 8;             // the same for the bulk-copy kernel (shared-memory stages)
+// Neighbour rows per trip for G lanes per row: rows of one or two lanes (16 or 32 bytes) hold
+// a trip's indices one per entry per lane, so they take half as many to stay in registers.
+constexpr int layer_chunk(int G) { return G >= 4 ? kChunk : (kChunk < 8 ? kChunk : 8); }
 
 // Build-time tuning of the register-load layer kernel (defaults are the measured best).
 #ifndef IGP_LAYER_MIN_CTAS
 #define IGP_LAYER_MIN_CTAS 2  // resident CTAs per SM the register budget is sized for
 #endif
-// L2 prefetch distance of the neighbour rows, in trips (0: no prefetch). The row loads of a
-// trip then find their lines in L2 instead of waiting on DRAM.
+// L2 prefetch distance of the neighbour rows, in trips, used when a layer's gathered slice of
+// T^(l-1) is larger than kL2ResidentBytes (the row loads of a trip then find their lines in L2
+// instead of waiting on DRAM); smaller slices stay in L2 and are not prefetched.
 #ifndef IGP_LAYER_PF
-#define IGP_LAYER_PF 2
+#define IGP_LAYER_PF 1
 #endif
+constexpr size_t kL2ResidentBytes = 96ull << 20;
 
 // Fetch the 128-byte line holding p into L2 (no data returned to the SM).
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -402,7 +411,7 @@ constexpr float kQScale = 1073741824.0f;  // 2^30
 // Rows are taken in `perm` order (NULL: their own order) in warp tiles of GPW rows, one
 // row per group of G lanes; with perm sorting rows by degree, the rows of a tile have
 // (nearly) equal degree and the groups run their gather loops in lockstep.
-template <int D, typename S>
+template <int D, typename S, int PF>
 __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const float* __restrict__ dinv,
     const float* __restrict__ wsum, const int32_t* __restrict__ perm, const S* __restrict__ Tin_all,
@@ -414,7 +423,7 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
   constexpr int VPL = Store<S>::VPL;
   constexpr int G = D / VPL;               // lanes per row
   constexpr int GPW = 32 / G;              // rows per warp tile
-  constexpr int C = kChunk;                // neighbour rows per trip
+  constexpr int C = layer_chunk(G);        // neighbour rows per trip
   constexpr int IPL = C >= G ? C / G : 1;  // trip indices held per lane
   static_assert(G >= 1 && G <= 32 && GPW * G == 32, "unsupported width");
   static_assert(C <= G || C % G == 0, "kChunk must be at most, or a multiple of, the lanes per row");
@@ -519,13 +528,13 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
       const int c = cur.b + tr * C;
       int jn[IPL];
       load_idx(jn, c + C, cur.e);
-#if IGP_LAYER_PF > 0
       // prefetch targets: this tile's trip tr + PF, and the next tile's trip tr (its first
       // PF trips; in decreasing-degree order the next tile has no more trips than this one)
       int pa[IPL], pb[IPL];
-      load_pf(pa, c + IGP_LAYER_PF * C, cur.e);
-      load_pf(pb, nxt.b + tr * C, tr < IGP_LAYER_PF ? nxt.e : 0);
-#endif
+      if (PF > 0) {
+        load_pf(pa, c + PF * C, cur.e);
+        load_pf(pb, nxt.b + tr * C, tr < PF ? nxt.e : 0);
+      }
       RT x[C];
 #pragma unroll
       for (int t = 0; t < C; ++t) {
@@ -534,10 +543,10 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
       }
 #pragma unroll
       for (int t = 0; t < C; ++t) RW::add(acc, x[t]);
-#if IGP_LAYER_PF > 0
-      prefetch_rows(pa);
-      prefetch_rows(pb);
-#endif
+      if (PF > 0) {
+        prefetch_rows(pa);
+        prefetch_rows(pb);
+      }
 #pragma unroll
       for (int k = 0; k < IPL; ++k) jw[k] = jn[k];
     }
@@ -637,7 +646,7 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
 // lanes then add the rows from shared memory. Waits are bounded (about a second); a
 // warp that gives up sets *err, waits (bounded) for its own copies and returns.
 constexpr int kTmaStages = 3;
-constexpr int kTmaStageBytes = 32 * kChunk * 16;  // rows per trip x row bytes, for any width
+constexpr int kTmaStageBytes = 32 * kTmaChunk * 16;  // rows per trip x row bytes, for any width
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -701,7 +710,7 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer_tma(
   constexpr int VPL = Store<S>::VPL;
   constexpr int G = D / VPL;               // lanes per row
   constexpr int GPW = 32 / G;              // rows per warp tile
-  constexpr int C = kChunk;                // neighbour rows per row per trip
+  constexpr int C = kTmaChunk;             // neighbour rows per row per trip
   constexpr int IPL = C >= G ? C / G : 1;  // trip entries held per lane
   constexpr int RB = D * (int)sizeof(S);   // bytes per row
   static_assert(GPW * C * RB == kTmaStageBytes, "stage size");
@@ -1152,7 +1161,7 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer_bat
   constexpr int VPL = Store<S>::VPL;
   constexpr int G = D / VPL;
   constexpr int GPW = 32 / G;
-  constexpr int C = kChunk;
+  constexpr int C = layer_chunk(G);
   constexpr int IPL = C >= G ? C / G : 1;
   static_assert(kBatchAlign % GPW == 0, "tiles must not straddle graphs");
 
@@ -1384,7 +1393,7 @@ struct LayerCfg {
     static std::atomic<int> v{0};  // filled once; concurrent server threads may race to fill it
     if (v == 0) {
       int b = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_layer<D, S>, kLayerThreads, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_layer<D, S, IGP_LAYER_PF>, kLayerThreads, 0);
       v = b > 0 ? b : 1;
     }
     return v;
@@ -1402,9 +1411,15 @@ struct LayerCfg {
 template <int D, typename S>
 igp_status layer_launch(const LayerArgs& a, cudaStream_t s) {
   dim3 gr(a.grid, a.d / D);
-  k_layer<D, S><<<gr, kLayerThreads, 0, s>>>(a.row_ptr, a.col, a.dinv, a.wsum, a.perm, (const S*)a.Tin,
-                                             (S*)a.Tout, a.stats_in, a.partials, a.stats_out, a.tickets, a.N, a.d,
-                                             a.alpha, a.theta, a.ddof);
+  if (a.prefetch)
+    k_layer<D, S, IGP_LAYER_PF><<<gr, kLayerThreads, 0, s>>>(a.row_ptr, a.col, a.dinv, a.wsum, a.perm,
+                                                             (const S*)a.Tin, (S*)a.Tout, a.stats_in, a.partials,
+                                                             a.stats_out, a.tickets, a.N, a.d, a.alpha, a.theta,
+                                                             a.ddof);
+  else
+    k_layer<D, S, 0><<<gr, kLayerThreads, 0, s>>>(a.row_ptr, a.col, a.dinv, a.wsum, a.perm, (const S*)a.Tin,
+                                                  (S*)a.Tout, a.stats_in, a.partials, a.stats_out, a.tickets, a.N,
+                                                  a.d, a.alpha, a.theta, a.ddof);
   return after_launch("k_layer");
 }
 
@@ -1792,6 +1807,7 @@ igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed
   la.err = err;
   la.withhold = o.reserved_test;
   la.gather4 = o.gather == IGP_GATHER_TMA4;
+  la.prefetch = (size_t)N * dc * sb > kL2ResidentBytes ? 1 : 0;
   la.N = N;
   la.d = d;
 
@@ -2115,6 +2131,7 @@ extern "C" igp_status igp_embed_noalloc(const int32_t* row_ptr, const int32_t* c
   la.err = err;
   la.withhold = 0;
   la.gather4 = 0;
+  la.prefetch = (size_t)N * d * sb > kL2ResidentBytes ? 1 : 0;
   la.N = N;
   la.d = d;
 

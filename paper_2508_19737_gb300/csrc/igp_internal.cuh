@@ -148,6 +148,7 @@ struct LayerArgs {
   int* err;       // device word set to 1 by a layer whose bounded wait ran out
   int withhold;   // test hook of the bounded wait (0 in normal use)
   int gather4;    // bulk-copy kernel: 1 = tile::gather4 through a tensor map
+  int prefetch;   // register-load kernel: 1 = L2 prefetch of the rows a few trips ahead
   int32_t N, d;
   float alpha, theta;
   int ddof, grid;
