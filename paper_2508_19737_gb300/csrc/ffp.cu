@@ -23,8 +23,8 @@
 //     indices and the next tiles' rows (perm entry two tiles ahead, row bounds, self
 //     row, dinv, w one tile ahead) are loaded during the current trip;
 //   * when the gathered slice of T^(l-1) is larger than L2 can hold, each trip also
-//     issues prefetch.global.L2 for the rows of the trip after next (and of the next
-//     tile's first trip), so that the register loads find their lines in L2;
+//     issues prefetch.global.L2 for the rows of the next trip (past the tile's last trip,
+//     the next tile's first), so that the register loads find their lines in L2;
 //   * column indices are loaded evict-first (streamed once); outputs stored streaming;
 //     bf16 neighbour rows are added with mixed-precision adds (one instruction a value);
 //   * wide rows can be split into column chunks (blockIdx.y) over a column-blocked
@@ -335,6 +335,7 @@ constexpr int layer_chunk(int G) { return G >= 4 ? kChunk : (kChunk < 8 ? kChunk
 #define IGP_LAYER_PF 1
 #endif
 constexpr size_t kL2ResidentBytes = 96ull << 20;
+constexpr int kClaimTiles = 8;  // tiles a warp claims at a time after its first
 
 // Fetch the 128-byte line holding p into L2 (no data returned to the SM).
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -406,7 +407,7 @@ constexpr float kQScale = 1073741824.0f;  // 2^30
 // blockIdx.y selects the chunk, whose N x D slice of T^(l-1) is one contiguous column
 // block of the activation layout and can stay in L2 while the chunk is processed.
 // Chunks are independent (tanh and the column statistics act per column); each has
-// its own partials and ticket.
+// its own column sums, ticket and tile counter.
 //
 // Rows are taken in `perm` order (NULL: their own order) in warp tiles of GPW rows, one
 // row per group of G lanes; with perm sorting rows by degree, the rows of a tile have
@@ -415,7 +416,7 @@ template <int D, typename S, int PF>
 __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const float* __restrict__ dinv,
     const float* __restrict__ wsum, const int32_t* __restrict__ perm, const S* __restrict__ Tin_all,
-    S* __restrict__ Tout_all, const float* __restrict__ stats_in, long long* __restrict__ partials_all,
+    S* __restrict__ Tout_all, const float* __restrict__ stats_in, unsigned long long* __restrict__ gsum_all,
     float* __restrict__ stats_out, unsigned* __restrict__ tickets, int32_t N, int32_t d, float alpha, float theta,
     int ddof) {
   using RW = Raw<S>;
@@ -438,8 +439,9 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
   const int64_t blk = (int64_t)blockIdx.y * N * D + lig * VPL;  // this lane's part of the column block
   const S* __restrict__ Tin = Tin_all + blk;
   S* __restrict__ Tout = Tout_all + blk;
-  long long* __restrict__ partials = partials_all + (int64_t)blockIdx.y * gridDim.x * 2 * D;
+  unsigned long long* __restrict__ gsum = gsum_all + (int64_t)blockIdx.y * 2 * D;
   unsigned* ticket = tickets + blockIdx.y;
+  unsigned* claims = tickets + gridDim.y + blockIdx.y;
   for (int c = threadIdx.x; c < D; c += blockDim.x) {
     s_mu[c] = stats_in ? stats_in[c0 + c] : 0.0f;
     s_is[c] = stats_in ? stats_in[d + c0 + c] : 1.0f;
@@ -451,9 +453,26 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
 #pragma unroll
   for (int v = 0; v < VPL; ++v) qs[v] = qq[v] = 0;
 
-  const int64_t ntiles = ((int64_t)N + GPW - 1) / GPW;
-  const int64_t nw = (int64_t)gridDim.x * kLayerWarps;
-  const int64_t w0 = (int64_t)blockIdx.x * kLayerWarps + warp;
+  // Tiles: warp w first takes tile w (in decreasing-degree order the heaviest tiles, one per
+  // warp), then claims chunks of kClaimTiles tiles from a counter, one chunk ahead of use,
+  // so that no warp is left with more than its share of the long rows.
+  // (tile ids fit 32 bits: ntiles <= N)
+  const int ntiles = (int)(((int64_t)N + GPW - 1) / GPW);
+  const int nw = gridDim.x * kLayerWarps;
+  const int w0 = blockIdx.x * kLayerWarps + warp;
+  auto claim = [&]() -> int {
+    unsigned c = 0;
+    if (lane == 0) c = atomicAdd(claims, 1u);
+    const int64_t t = nw + (int64_t)__shfl_sync(0xffffffffu, c, 0) * kClaimTiles;
+    return t < ntiles ? (int)t : ntiles;
+  };
+  int next_chunk = claim();
+  auto next_tile = [&](int t) -> int {  // the tile after t in this warp's sequence
+    if (t >= nw && (t - nw + 1) % kClaimTiles) return t + 1;
+    const int c = next_chunk;
+    if (c < ntiles) next_chunk = claim();
+    return c;
+  };
 
   // lane lig holds trip entries lig + G k (k < IPL) counted from `base`, below `end`
   auto load_idx = [&](int (&jw)[IPL], int base, int end) {
@@ -463,8 +482,8 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
       jw[k] = (t < C && base + t < end) ? ld_stream(col + base + t, pol_first) : 0;
     }
   };
-  auto row_at = [&](int64_t tile) -> int {
-    const int64_t p = tile * GPW + grp;
+  auto row_at = [&](int tile) -> int {
+    const int64_t p = (int64_t)tile * GPW + grp;
     if (tile >= ntiles || p >= N) return -1;
     return perm ? __ldg(perm + p) : (int)p;
   };
@@ -511,11 +530,13 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
   int r = row_at(w0);
   RowData cur;
   fetch_row(r, cur);
-  int r_n = row_at(w0 + nw);
+  int tn = next_tile(w0);
+  int r_n = row_at(tn);
   int jw[IPL];
   load_idx(jw, cur.b, cur.e);
-  for (int64_t tile = w0; tile < ntiles; tile += nw) {
-    const int r_nn = row_at(tile + 2 * nw);
+  for (int tile = w0; tile < ntiles;) {
+    const int tnn = next_tile(tn);
+    const int r_nn = row_at(tnn);
     RowData nxt;
     fetch_row(r_n, nxt);
 
@@ -528,12 +549,15 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
       const int c = cur.b + tr * C;
       int jn[IPL];
       load_idx(jn, c + C, cur.e);
-      // prefetch targets: this tile's trip tr + PF, and the next tile's trip tr (its first
-      // PF trips; in decreasing-degree order the next tile has no more trips than this one)
-      int pa[IPL], pb[IPL];
+      // prefetch target: trip tr + PF of this tile, or past its last trip the next tile's
+      // trip (tr + PF - mtrip)
+      int pa[IPL];
       if (PF > 0) {
-        load_pf(pa, c + PF * C, cur.e);
-        load_pf(pb, nxt.b + tr * C, tr < PF ? nxt.e : 0);
+        const int q = tr + PF;
+        if (q < mtrip)
+          load_pf(pa, c + PF * C, cur.e);
+        else
+          load_pf(pa, nxt.b + (q - mtrip) * C, nxt.e);
       }
       RT x[C];
 #pragma unroll
@@ -543,10 +567,7 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
       }
 #pragma unroll
       for (int t = 0; t < C; ++t) RW::add(acc, x[t]);
-      if (PF > 0) {
-        prefetch_rows(pa);
-        prefetch_rows(pb);
-      }
+      if (PF > 0) prefetch_rows(pa);
 #pragma unroll
       for (int k = 0; k < IPL; ++k) jw[k] = jn[k];
     }
@@ -576,6 +597,8 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
     r = r_n;
     r_n = r_nn;
     cur = nxt;
+    tile = tn;
+    tn = tnn;
   }
 
   // ---- column statistics: exact integer sums over groups, warps, CTAs
@@ -595,11 +618,12 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
     }
   }
   __syncthreads();
+  // this CTA's sums are added to the chunk's global int64 sums (exact, in any order)
   for (int c = threadIdx.x; c < 2 * D; c += blockDim.x) {
     long long a = 0;
 #pragma unroll
     for (int w = 0; w < kLayerWarps; ++w) a += s_red[w][c];
-    partials[(int64_t)blockIdx.x * 2 * D + c] = a;
+    atomicAdd(gsum + c, (unsigned long long)a);
   }
   __threadfence();
   __syncthreads();
@@ -607,22 +631,8 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  constexpr int R0 = kLayerThreads / (2 * D) > 0 ? kLayerThreads / (2 * D) : 1;
-  constexpr int R = R0 < kLayerWarps ? R0 : kLayerWarps;
-  long long* s_tot = &s_red[0][0];  // reuse: R * 2D <= kLayerWarps * 2D
-  for (int t = threadIdx.x; t < R * 2 * D; t += blockDim.x) {
-    const int c = t % (2 * D), rr = t / (2 * D);
-    long long a = 0;
-    for (int b = rr; b < (int)gridDim.x; b += R) a += __ldcg(partials + (int64_t)b * 2 * D + c);
-    s_tot[rr * 2 * D + c] = a;
-  }
-  __syncthreads();
   for (int c = threadIdx.x; c < D; c += blockDim.x) {
-    long long sa = 0, qa = 0;
-    for (int rr = 0; rr < R; ++rr) {
-      sa += s_tot[rr * 2 * D + c];
-      qa += s_tot[rr * 2 * D + D + c];
-    }
+    const long long sa = (long long)__ldcg(gsum + c), qa = (long long)__ldcg(gsum + D + c);
     const double n = (double)N;
     const double st = (double)sa * (1.0 / (double)(1ll << kQBits));  // sum of t
     const double sq = (double)qa * (1.0 / (double)(1ll << kQBits));  // sum of t^2
@@ -634,7 +644,12 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
     stats_out[c0 + c] = (float)mean;
     stats_out[d + c0 + c] = sd > 0.0 ? (float)(1.0 / sd) : 0.0f;
   }
-  if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
+  __syncthreads();  // every read of gsum precedes its reset
+  for (int c = threadIdx.x; c < 2 * D; c += blockDim.x) gsum[c] = 0ull;
+  if (threadIdx.x == 0) {  // ready for the next launch
+    *ticket = 0u;
+    *claims = 0u;
+  }
 }
 
 // ------------------------------------------------------------------ Eq. 4 layer, bulk-copy gathers
@@ -702,7 +717,7 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer_tma(
     const __grid_constant__ CUtensorMap tmap, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
     const float* __restrict__ dinv, const float* __restrict__ wsum, const int32_t* __restrict__ perm,
     const S* __restrict__ Tin_all,
-    S* __restrict__ Tout_all, const float* __restrict__ stats_in, long long* __restrict__ partials_all,
+    S* __restrict__ Tout_all, const float* __restrict__ stats_in, unsigned long long* __restrict__ gsum_all,
     float* __restrict__ stats_out, unsigned* __restrict__ tickets, int* __restrict__ err, int32_t N, int32_t d,
     float alpha, float theta, int ddof, int withhold) {
   using RW = Raw<S>;
@@ -729,7 +744,7 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer_tma(
   if (threadIdx.x == 0) s_fail = 0;
   const S* __restrict__ Tin = Tin_all + blk;  // row r of this column block at Tin + r * D
   S* __restrict__ Tout = Tout_all + blk + lig * VPL;
-  long long* __restrict__ partials = partials_all + (int64_t)blockIdx.y * gridDim.x * 2 * D;
+  unsigned long long* __restrict__ gsum = gsum_all + (int64_t)blockIdx.y * 2 * D;
   unsigned* ticket = tickets + blockIdx.y;
   const uint32_t ring = smem_addr(dyn) + warp * kTmaStages * kTmaStageBytes;
   const uint32_t mbar0 = smem_addr(dyn) + kLayerWarps * kTmaStages * kTmaStageBytes + warp * kTmaStages * 8;
@@ -984,11 +999,12 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer_tma(
   }
   __syncthreads();
   if (s_fail) return;  // uniform over the CTA
+  // this CTA's sums are added to the chunk's global int64 sums (exact, in any order)
   for (int c = threadIdx.x; c < 2 * D; c += blockDim.x) {
     long long a = 0;
 #pragma unroll
     for (int w = 0; w < kLayerWarps; ++w) a += s_red[w][c];
-    partials[(int64_t)blockIdx.x * 2 * D + c] = a;
+    atomicAdd(gsum + c, (unsigned long long)a);
   }
   __threadfence();
   __syncthreads();
@@ -996,22 +1012,8 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer_tma(
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  constexpr int R0 = kLayerThreads / (2 * D) > 0 ? kLayerThreads / (2 * D) : 1;
-  constexpr int R = R0 < kLayerWarps ? R0 : kLayerWarps;
-  long long* s_tot = &s_red[0][0];  // reuse: R * 2D <= kLayerWarps * 2D
-  for (int t = threadIdx.x; t < R * 2 * D; t += blockDim.x) {
-    const int c = t % (2 * D), rr = t / (2 * D);
-    long long a = 0;
-    for (int b = rr; b < (int)gridDim.x; b += R) a += __ldcg(partials + (int64_t)b * 2 * D + c);
-    s_tot[rr * 2 * D + c] = a;
-  }
-  __syncthreads();
   for (int c = threadIdx.x; c < D; c += blockDim.x) {
-    long long sa = 0, qa = 0;
-    for (int rr = 0; rr < R; ++rr) {
-      sa += s_tot[rr * 2 * D + c];
-      qa += s_tot[rr * 2 * D + D + c];
-    }
+    const long long sa = (long long)__ldcg(gsum + c), qa = (long long)__ldcg(gsum + D + c);
     const double n = (double)N;
     const double st = (double)sa * (1.0 / (double)(1ll << kQBits));  // sum of t
     const double sq = (double)qa * (1.0 / (double)(1ll << kQBits));  // sum of t^2
@@ -1023,6 +1025,8 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer_tma(
     stats_out[c0 + c] = (float)mean;
     stats_out[d + c0 + c] = sd > 0.0 ? (float)(1.0 / sd) : 0.0f;
   }
+  __syncthreads();  // every read of gsum precedes its reset
+  for (int c = threadIdx.x; c < 2 * D; c += blockDim.x) gsum[c] = 0ull;
   if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
 }
 
@@ -1413,12 +1417,12 @@ igp_status layer_launch(const LayerArgs& a, cudaStream_t s) {
   dim3 gr(a.grid, a.d / D);
   if (a.prefetch)
     k_layer<D, S, IGP_LAYER_PF><<<gr, kLayerThreads, 0, s>>>(a.row_ptr, a.col, a.dinv, a.wsum, a.perm,
-                                                             (const S*)a.Tin, (S*)a.Tout, a.stats_in, a.partials,
+                                                             (const S*)a.Tin, (S*)a.Tout, a.stats_in, a.gsum,
                                                              a.stats_out, a.tickets, a.N, a.d, a.alpha, a.theta,
                                                              a.ddof);
   else
     k_layer<D, S, 0><<<gr, kLayerThreads, 0, s>>>(a.row_ptr, a.col, a.dinv, a.wsum, a.perm, (const S*)a.Tin,
-                                                  (S*)a.Tout, a.stats_in, a.partials, a.stats_out, a.tickets, a.N,
+                                                  (S*)a.Tout, a.stats_in, a.gsum, a.stats_out, a.tickets, a.N,
                                                   a.d, a.alpha, a.theta, a.ddof);
   return after_launch("k_layer");
 }
@@ -1502,13 +1506,13 @@ igp_status layer_tma_launch(const LayerArgs& a, cudaStream_t s) {
     IGP_TRY_CUDA(
         cudaFuncSetAttribute(k_layer_tma<D, S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaDynSmem));
     k_layer_tma<D, S, 4><<<gr, kLayerThreads, kTmaDynSmem, s>>>(
-        m, a.row_ptr, a.col, a.dinv, a.wsum, a.perm, (const S*)a.Tin, (S*)a.Tout, a.stats_in, a.partials, a.stats_out,
+        m, a.row_ptr, a.col, a.dinv, a.wsum, a.perm, (const S*)a.Tin, (S*)a.Tout, a.stats_in, a.gsum, a.stats_out,
         a.tickets, a.err, a.N, a.d, a.alpha, a.theta, a.ddof, a.withhold);
   } else {
     IGP_TRY_CUDA(
         cudaFuncSetAttribute(k_layer_tma<D, S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaDynSmem));
     k_layer_tma<D, S, 1><<<gr, kLayerThreads, kTmaDynSmem, s>>>(
-        m, a.row_ptr, a.col, a.dinv, a.wsum, a.perm, (const S*)a.Tin, (S*)a.Tout, a.stats_in, a.partials, a.stats_out,
+        m, a.row_ptr, a.col, a.dinv, a.wsum, a.perm, (const S*)a.Tin, (S*)a.Tout, a.stats_in, a.gsum, a.stats_out,
         a.tickets, a.err, a.N, a.d, a.alpha, a.theta, a.ddof, a.withhold);
   }
   return after_launch("k_layer_tma");
@@ -1762,12 +1766,12 @@ igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed
     return IGP_E_INVAL;
   }
   const int grid = tma ? lops.tma_grid(N) : lops.grid(N);
-  // workspace: T0 | T1 | stats[2][2d] | partials[nchunks][grid][2dc] | err, tickets[nchunks]
+  // workspace: T0 | T1 | stats[2][2d] | gsum[nchunks][2dc] | err, tickets[nchunks], claims[nchunks]
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t bT = al((size_t)N * d * sb);
   const size_t bS = al(2 * 2 * (size_t)d * sizeof(float));
-  const size_t bP = al((size_t)nchunks * grid * 2 * dc * sizeof(long long));
-  const size_t bK = al((size_t)(nchunks + 1) * sizeof(unsigned));
+  const size_t bP = al((size_t)nchunks * 2 * dc * sizeof(unsigned long long));
+  const size_t bK = al((size_t)(2 * nchunks + 1) * sizeof(unsigned));
   const size_t need = 2 * bT + bS + bP + bK;
   if (g->ws_bytes < need) {
     if (g->ws) dev_free(g->ws, s);
@@ -1782,10 +1786,10 @@ igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed
   void* T0 = base;
   void* T1 = base + bT;
   float* stats = (float*)(base + 2 * bT);
-  long long* partials = (long long*)(base + 2 * bT + bS);
+  unsigned long long* gsum = (unsigned long long*)(base + 2 * bT + bS);
   int* err = (int*)(base + 2 * bT + bS + bP);
   unsigned* tickets = (unsigned*)(err + 1);
-  IGP_TRY_CUDA(cudaMemsetAsync(err, 0, (nchunks + 1) * sizeof(unsigned), s));
+  IGP_TRY_CUDA(cudaMemsetAsync(gsum, 0, bP + (2 * nchunks + 1) * sizeof(unsigned), s));
 
   {
     PhaseTimer pt(prof, IGP_PHASE_THETA, s);
@@ -1802,7 +1806,7 @@ igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed
   la.perm = g->perm;
   la.dinv = g->dinv;
   la.wsum = g->wsum;
-  la.partials = partials;
+  la.gsum = gsum;
   la.tickets = tickets;
   la.err = err;
   la.withhold = o.reserved_test;
@@ -2083,14 +2087,14 @@ extern "C" igp_status igp_embed_noalloc(const int32_t* row_ptr, const int32_t* c
     set_error("igp_embed_noalloc: row_ptr, col, out (and opts->x_in) must be device memory");
     return IGP_E_INVAL;
   }
-  // scratch layout: dinv | w | T0 | T1 | stats[2][2d] | partials[grid][2d] | ticket
+  // scratch layout: dinv | w | T0 | T1 | stats[2][2d] | gsum[2d] | ticket, claims, err
   const size_t sb = o.storage == IGP_STORE_BF16 ? 2 : 4;
   const int grid = ops.grid(N);
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t bN = al((size_t)N * 4);
   const size_t bT = al((size_t)N * d * sb);
   const size_t bS = al(2 * 2 * (size_t)d * sizeof(float));
-  const size_t bP = al((size_t)grid * 2 * d * sizeof(long long));
+  const size_t bP = al((size_t)2 * d * sizeof(unsigned long long));
   const size_t need = 2 * bN + 2 * bT + bS + bP + 256;
   if (need > kNoAllocScratchBytes) {
     set_error("igp_embed_noalloc: N=%d, d=%d needs %zu bytes of scratch, more than the fixed %zu (16 MiB); "
@@ -2107,10 +2111,10 @@ extern "C" igp_status igp_embed_noalloc(const int32_t* row_ptr, const int32_t* c
   void* T0 = base + 2 * bN;
   void* T1 = base + 2 * bN + bT;
   float* stats = (float*)(base + 2 * bN + 2 * bT);
-  long long* partials = (long long*)(base + 2 * bN + 2 * bT + bS);
-  unsigned* ticket = (unsigned*)(base + 2 * bN + 2 * bT + bS + bP);
-  int* err = (int*)(ticket + 1);
-  IGP_TRY_CUDA(cudaMemsetAsync(ticket, 0, 2 * sizeof(unsigned), s));
+  unsigned long long* gsum = (unsigned long long*)(base + 2 * bN + 2 * bT + bS);
+  unsigned* ticket = (unsigned*)(base + 2 * bN + 2 * bT + bS + bP);  // ticket, tile-claim counter
+  int* err = (int*)(ticket + 2);
+  IGP_TRY_CUDA(cudaMemsetAsync(gsum, 0, bP + 3 * sizeof(unsigned), s));
 
   // the caller's graph as it is (no relabelling: that would need memory)
   IGP_TRY(launch_dinv_wsum(row_ptr, col, N, tau, o.eps, dinv, wsum, s));
@@ -2126,7 +2130,7 @@ extern "C" igp_status igp_embed_noalloc(const int32_t* row_ptr, const int32_t* c
   la.perm = nullptr;  // rows in their own order
   la.dinv = dinv;
   la.wsum = wsum;
-  la.partials = partials;
+  la.gsum = gsum;
   la.tickets = ticket;
   la.err = err;
   la.withhold = 0;

@@ -142,9 +142,9 @@ struct LayerArgs {
   const void* Tin;
   void* Tout;
   const float* stats_in;
-  long long* partials;
+  unsigned long long* gsum;  // per column chunk [2 dc] int64 column sums, zero on entry (left zero)
   float* stats_out;
-  unsigned* tickets;
+  unsigned* tickets;  // [2 nchunks]: finish tickets, then tile-claim counters; zero on entry (left zero)
   int* err;       // device word set to 1 by a layer whose bounded wait ran out
   int withhold;   // test hook of the bounded wait (0 in normal use)
   int gather4;    // bulk-copy kernel: 1 = tile::gather4 through a tensor map
