@@ -43,7 +43,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="dcsbm-2m", choices=sorted(synth.WORKLOADS) + sorted(synth.BATCH_WORKLOADS) + sorted(synth.SERVE_WORKLOADS))
-    p.add_argument("--slots", type=int, default=4, help="concurrent requests of the served stream")
+    p.add_argument("--slots", type=int, default=8, help="concurrent requests of the served stream")
+    p.add_argument("--batch-rows", type=int, default=0,
+                   help="served graphs with fewer nodes share batched FFPs (0: every slot embeds its own)")
     p.add_argument("--d", type=int, default=None, help="override the workload's embedding width")
     p.add_argument("--storage", default=None, choices=[None, "f32", "bf16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -367,7 +369,7 @@ def run_serve(args):
     slots = args.slots
     # warm-up: a few requests of the smallest graph
     kmin = int(np.argmin(nfinal))
-    sv = api.Server(slots=slots)
+    sv = api.Server(slots=slots, batch_rows=args.batch_rows)
     for _ in range(max(args.warmup, 3)):
         sv.wait(submit(sv, kmin, 0, storage, 0))
     sv.close()
@@ -376,7 +378,7 @@ def run_serve(args):
     clocks = ClockSampler(local)
     clocks.start()
     n0 = api.launch_count()
-    sv = api.Server(slots=slots)
+    sv = api.Server(slots=slots, batch_rows=args.batch_rows)
     tickets = [None] * R
     t0 = time.perf_counter()
     for r, (k, t) in enumerate(order):
@@ -397,12 +399,13 @@ def run_serve(args):
     sv.close()
 
     # (2) saturation: every request queued at once, same order
-    sv = api.Server(slots=slots)
+    sv = api.Server(slots=slots, batch_rows=args.batch_rows)
     t0 = time.perf_counter()
     tickets = [submit(sv, k, t, storage, 1000 * k + t) for k, t in order]
     for tk in tickets:
         sv.wait(tk)
     t_sat = time.perf_counter() - t0
+    st_sat = sv.stats()
     sv.close()
     clk = clocks.stop()
 
@@ -429,17 +432,19 @@ def run_serve(args):
         "steps": R, "warmup": max(args.warmup, 3), "ms_per_step": t_sat / R * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
         "config": {"workload": args.workload, **params, "d": d, "tau": tau, "L": L, "storage": storage,
-                   "slots": slots, "requests": R, "N_total_final": int(sum(nfinal)),
+                   "slots": slots, "batch_rows": args.batch_rows, "requests": R, "N_total_final": int(sum(nfinal)),
                    "step": "one snapshot request: increment merge (or CSR build) + FFP + result to host",
                    "l2": "per-request working sets up to the largest graph; not flushed between requests"},
         "edge_dim_layer_per_s": units / t_sat,
         "open_loop": {"rate_offered": params["rate"], "wall_s": t_open, "rate_achieved": R / t_open,
                       "snapshot_latency_p50_s": pct(lat, 50), "snapshot_latency_p99_s": pct(lat, 99),
                       "graph_latency_p50_s": pct(per_graph, 50), "graph_latency_p99_s": pct(per_graph, 99),
-                      "server_p50_s": st_open["latency_p50_s"], "server_p99_s": st_open["latency_p99_s"]},
+                      "server_p50_s": st_open["latency_p50_s"], "server_p99_s": st_open["latency_p99_s"],
+                      "shared_batches": st_open["batches"], "requests_in_shared_batches": st_open["batched"]},
         "serial_fp32": {"value": R / t_ser32, "unit": "requests/s", "wall_s": t_ser32},
         f"serial_{storage}": {"value": R / t_ser, "unit": "requests/s", "wall_s": t_ser},
         "speedup_vs_serial_fp32": t_ser32 / t_sat,
+        "saturation": {"shared_batches": st_sat["batches"], "requests_in_shared_batches": st_sat["batched"]},
         "gpu_launches": int(launches_open),
         "clocks": clk,
     }

@@ -54,7 +54,9 @@ typedef int32_t igp_status;
 #define IGP_STORE_F32  0
 #define IGP_STORE_BF16 1
 
-/* How a layer brings neighbour rows to the SM (igp_embed_opts.gather). Result-neutral. */
+/* How a layer brings neighbour rows to the SM (igp_embed_opts.gather). The bulk-copy modes add each
+ * row's neighbours in one sequence; the register-load mode gathers rows of a few hundred entries
+ * or more with a whole warp (another fp32 summation order), so the modes agree to fp32 rounding. */
 #define IGP_GATHER_AUTO 0  /* the measured best (currently register loads for every width) */
 #define IGP_GATHER_LSU  1  /* 16-byte register loads by the lanes of each row group */
 #define IGP_GATHER_BULK 2  /* one cp.async.bulk copy per row into a per-warp shared-memory ring */
@@ -84,7 +86,9 @@ typedef struct igp_embed_opts {
   int32_t chunk_cols;  /* columns per layer pass; 0 (default) picks the widest of d, d/2, d/4, ..
                           whose N x width slice of the activations fits ~72 MB of L2, keeping at
                           least 128 bytes per row. Otherwise a power of two dividing d, >= 8, with
-                          at least 16 bytes per row. Result-neutral (exact integer statistics). */
+                          at least 16 bytes per row. The statistics are exact integer sums; the
+                          fp32 summation order of the highest-degree rows depends on the pass
+                          width, so passes change results only by fp32 rounding. */
   int32_t gather;      /* IGP_GATHER_AUTO (default), _LSU, _BULK or _TMA4 */
   int32_t reserved_test;/* 0. (Non-zero only in the library's own test of its bounded device waits.) */
   const void* x_in;    /* NULL: Theta from `seed`. Else a DEVICE pointer to N x d row-major values in
@@ -179,7 +183,9 @@ igp_status igp_embed(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t se
 /*
  * Batches: many independent graphs embedded together (block-diagonal packing). Each graph keeps its
  * own Theta seed and its own ZNorm column statistics (Eq. 4 acts per graph), so every graph's
- * result equals igp_embed on that graph alone, bit for bit.
+ * result equals igp_embed on that graph alone, to fp32 rounding (igp_embed gathers a graph's
+ * highest-degree rows with a whole warp, in another summation order; every other row and the
+ * column statistics are computed identically).
  *
  * igp_batch_create: packs G built graphs (copied; the graphs may be freed afterwards) into one
  *   device CSR, with each graph's rows by decreasing degree as the processing order. Synchronises
@@ -216,7 +222,13 @@ void igp_batch_free(igp_batch* b);
  * memory is not there). Requests are picked in submission order among those that may start. Resident graphs keep
  * their CSR and degree state on the device between requests (streaming, Alg. 2): an
  * IGP_REQ_APPEND request grows a resident graph by an edge increment and re-embeds it; requests
- * on the same graph_id run in submission order. Results do not depend on what else runs.
+ * on the same graph_id run in submission order. The slots build or grow the requests' CSRs and
+ * embed the graphs, each on its own stream, so admitted requests overlap on the device. With
+ * batch_rows > 0 the FFPs of graphs with fewer nodes are batched instead: one batcher thread takes
+ * every such request whose CSR is ready when it frees up and embeds those with the same (tau, L, d,
+ * options) together in one block-diagonal batch (one launch sequence). Results do not depend on
+ * what else runs: each equals igp_embed of that graph alone (bit for bit when embedded by its
+ * slot, to fp32 rounding when embedded in a shared batch).
  */
 typedef struct igp_server igp_server;
 
@@ -225,7 +237,7 @@ typedef struct igp_server_opts {
   int32_t max_queue;      /* queued requests allowed (0: no limit); 0 */
   int64_t reserve_bytes;  /* device memory left free; 1 GiB */
   int32_t device;         /* CUDA device (-1: the current one); -1 */
-  int32_t reserved0;
+  int32_t batch_rows;     /* graphs of fewer nodes are embedded in shared batches (0: never); 0 */
 } igp_server_opts;
 
 #define IGP_REQ_EMBED  0  /* build a graph from the edges (N nodes) and embed it */
@@ -261,6 +273,8 @@ typedef struct igp_server_stats {
   int64_t budget_bytes;    /* free device memory at igp_server_create minus reserve_bytes */
   double latency_p50_s, latency_p99_s;  /* submit-to-done latency of completed requests */
   int64_t resident_bytes;  /* device bytes held by resident graphs */
+  int64_t batches;         /* FFP launch sequences that served two or more requests together */
+  int64_t batched;         /* requests embedded in such shared batches */
 } igp_server_stats;
 
 /* Defaults as listed in igp_server_opts. */

@@ -68,7 +68,7 @@ class EmbedOpts(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("max_queue", ctypes.c_int32), ("reserve_bytes", ctypes.c_int64),
-                ("device", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("batch_rows", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -83,7 +83,7 @@ class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "cancelled", "queued", "running",
                                               "resident_graphs", "admitted_bytes", "budget_bytes")] + \
                [("latency_p50_s", ctypes.c_double), ("latency_p99_s", ctypes.c_double),
-                ("resident_bytes", ctypes.c_int64)]
+                ("resident_bytes", ctypes.c_int64), ("batches", ctypes.c_int64), ("batched", ctypes.c_int64)]
 
 
 IGP_REQ_EMBED = 0
@@ -407,10 +407,11 @@ class Batch:
 class Server:
     """Owning wrapper of an igp_server: queued, memory-admitted, concurrent embed / append requests."""
 
-    def __init__(self, slots=4, max_queue=0, reserve_bytes=1 << 30, device=-1):
+    def __init__(self, slots=4, max_queue=0, reserve_bytes=1 << 30, device=-1, batch_rows=0):
         o = ServerOpts()
         lib().igp_server_opts_init(ctypes.byref(o))
         o.slots, o.max_queue, o.reserve_bytes, o.device = slots, max_queue, reserve_bytes, device
+        o.batch_rows = batch_rows
         h = ctypes.c_void_p()
         _check(lib().igp_server_create(ctypes.byref(o), ctypes.byref(h)))
         self.handle = h.value

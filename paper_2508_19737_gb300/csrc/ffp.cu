@@ -403,6 +403,14 @@ struct Raw<__nv_bfloat16> {
 constexpr int kQBits = 30;
 constexpr float kQScale = 1073741824.0f;  // 2^30
 
+// Heavy rows: in the single-graph layer, rows of at least layer_heavy_min(G) entries (they
+// lead the degree order) are gathered by the whole warp, one row per tile, so that no warp is
+// left with a chain of trips longer than the rest of the layer: the row's entries are cut into
+// chunks of C, group g (of the warp's GPW groups) adds chunks g, g + GPW, g + 2 GPW, .. in order,
+// and the groups' sums are combined by an xor tree over the group bits. (Other paths add every
+// row's entries in one sequence, so they agree with it to fp32 rounding.)
+constexpr int layer_heavy_min(int G) { return 32 / G > 1 ? (32 / G) * layer_chunk(G) * 4 : 1 << 30; }
+
 // Columns are processed in chunks of D (the template width) out of d per row:
 // blockIdx.y selects the chunk, whose N x D slice of T^(l-1) is one contiguous column
 // block of the activation layout and can stay in L2 while the chunk is processed.
@@ -417,8 +425,8 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const float* __restrict__ dinv,
     const float* __restrict__ wsum, const int32_t* __restrict__ perm, const S* __restrict__ Tin_all,
     S* __restrict__ Tout_all, const float* __restrict__ stats_in, unsigned long long* __restrict__ gsum_all,
-    float* __restrict__ stats_out, unsigned* __restrict__ tickets, int32_t N, int32_t d, float alpha, float theta,
-    int ddof) {
+    float* __restrict__ stats_out, unsigned* __restrict__ tickets, const int* __restrict__ heavy_count, int32_t N,
+    int32_t d, float alpha, float theta, int ddof) {
   using RW = Raw<S>;
   using RT = typename RW::T;
   constexpr int VPL = Store<S>::VPL;
@@ -456,8 +464,10 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
   // Tiles: warp w first takes tile w (in decreasing-degree order the heaviest tiles, one per
   // warp), then claims chunks of kClaimTiles tiles from a counter, one chunk ahead of use,
   // so that no warp is left with more than its share of the long rows.
-  // (tile ids fit 32 bits: ntiles <= N)
-  const int ntiles = (int)(((int64_t)N + GPW - 1) / GPW);
+  // The first H rows of the order (the heavy ones, with perm) are one tile each, gathered by
+  // the whole warp; the rest go GPW to a tile. (Tile ids fit 32 bits: ntiles <= N.)
+  const int H = heavy_count ? __ldg(heavy_count) : 0;
+  const int ntiles = H + (int)(((int64_t)N - H + GPW - 1) / GPW);
   const int nw = gridDim.x * kLayerWarps;
   const int w0 = blockIdx.x * kLayerWarps + warp;
   auto claim = [&]() -> int {
@@ -483,8 +493,10 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
     }
   };
   auto row_at = [&](int tile) -> int {
-    const int64_t p = (int64_t)tile * GPW + grp;
-    if (tile >= ntiles || p >= N) return -1;
+    if (tile >= ntiles) return -1;
+    if (tile < H) return __ldg(perm + tile);
+    const int64_t p = H + (int64_t)(tile - H) * GPW + grp;
+    if (p >= N) return -1;
     return perm ? __ldg(perm + p) : (int)p;
   };
   struct RowData {
@@ -533,31 +545,35 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
   int tn = next_tile(w0);
   int r_n = row_at(tn);
   int jw[IPL];
-  load_idx(jw, cur.b, cur.e);
+  load_idx(jw, cur.b + (w0 < H ? grp * C : 0), cur.e);
   for (int tile = w0; tile < ntiles;) {
     const int tnn = next_tile(tn);
     const int r_nn = row_at(tnn);
     RowData nxt;
     fetch_row(r_n, nxt);
 
-    const int ntrip = (cur.e - cur.b + C - 1) / C;
+    // A heavy tile is one row gathered by all groups (group g takes chunks g, g + GPW, .. of C
+    // entries, then an xor tree adds the groups' sums); otherwise every group gathers its own
+    // row, C entries a trip, in lockstep.
+    const bool heavy = tile < H;  // warp-uniform
+    const int cstep = heavy ? GPW * C : C;  // entries between a group's trips
+    const int ntrip = heavy ? ((cur.e - cur.b + C - 1) / C + GPW - 1) / GPW : (cur.e - cur.b + C - 1) / C;
     const int mtrip = __reduce_max_sync(0xffffffffu, ntrip);
     float acc[VPL];
 #pragma unroll
     for (int v = 0; v < VPL; ++v) acc[v] = 0.0f;
     for (int tr = 0; tr < mtrip; ++tr) {
-      const int c = cur.b + tr * C;
+      const int c = cur.b + (heavy ? grp * C : 0) + tr * cstep;
       int jn[IPL];
-      load_idx(jn, c + C, cur.e);
+      load_idx(jn, c + cstep, cur.e);
       // prefetch target: trip tr + PF of this tile, or past its last trip the next tile's
-      // trip (tr + PF - mtrip)
+      // first trip
       int pa[IPL];
       if (PF > 0) {
-        const int q = tr + PF;
-        if (q < mtrip)
-          load_pf(pa, c + PF * C, cur.e);
+        if (tr + PF < mtrip)
+          load_pf(pa, c + PF * cstep, cur.e);
         else
-          load_pf(pa, nxt.b + (q - mtrip) * C, nxt.e);
+          load_pf(pa, nxt.b + (tn < H ? grp * C : 0), nxt.e);
       }
       RT x[C];
 #pragma unroll
@@ -571,9 +587,17 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
 #pragma unroll
       for (int k = 0; k < IPL; ++k) jw[k] = jn[k];
     }
-    // first trip indices of the next tile, then this tile's epilogue
-    load_idx(jw, nxt.b, nxt.e);
-    if (r >= 0) {
+    if (heavy) {
+#pragma unroll
+      for (int m = G; m < 32; m <<= 1) {
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], m);
+      }
+    }
+    // first trip indices of the next tile, then this tile's epilogue (a heavy tile's by its
+    // first group)
+    load_idx(jw, nxt.b + (tn < H ? grp * C : 0), nxt.e);
+    if (r >= 0 && (!heavy || grp == 0)) {
       float sv[VPL];
       RW::unpack(cur.self, sv);
       const bool scaled = cur.di > 0.0f;
@@ -1418,12 +1442,12 @@ igp_status layer_launch(const LayerArgs& a, cudaStream_t s) {
   if (a.prefetch)
     k_layer<D, S, IGP_LAYER_PF><<<gr, kLayerThreads, 0, s>>>(a.row_ptr, a.col, a.dinv, a.wsum, a.perm,
                                                              (const S*)a.Tin, (S*)a.Tout, a.stats_in, a.gsum,
-                                                             a.stats_out, a.tickets, a.N, a.d, a.alpha, a.theta,
-                                                             a.ddof);
+                                                             a.stats_out, a.tickets, a.heavy_count, a.N, a.d,
+                                                             a.alpha, a.theta, a.ddof);
   else
     k_layer<D, S, 0><<<gr, kLayerThreads, 0, s>>>(a.row_ptr, a.col, a.dinv, a.wsum, a.perm, (const S*)a.Tin,
-                                                  (S*)a.Tout, a.stats_in, a.gsum, a.stats_out, a.tickets, a.N,
-                                                  a.d, a.alpha, a.theta, a.ddof);
+                                                  (S*)a.Tout, a.stats_in, a.gsum, a.stats_out, a.tickets,
+                                                  a.heavy_count, a.N, a.d, a.alpha, a.theta, a.ddof);
   return after_launch("k_layer");
 }
 
@@ -1676,24 +1700,26 @@ igp_status launch_dinv_wsum(const int32_t* row_ptr, const int32_t* col, int32_t 
 
 }  // namespace
 
-// Rows by decreasing degree (g->perm), once per graph.
+// Rows by decreasing degree (g->perm), once per graph. The allocation holds perm[N] and after
+// it the offsets off[k] (k = 0..max_deg + 1) of each degree key in perm: off[k] = number of rows
+// of degree > max_deg - k, so the rows of degree >= T are perm[0 .. off[max_deg - T + 1]).
 igp_status ensure_perm(igp_graph* g, cudaStream_t s) {
   if (g->perm) return IGP_OK;
   const int32_t N = g->N;
   const int64_t nb = (int64_t)g->max_deg + 1;
   void* p = nullptr;
-  IGP_TRY(dev_alloc(&p, (size_t)N * sizeof(int32_t), s));
+  IGP_TRY(dev_alloc(&p, ((size_t)N + nb + 1) * sizeof(int32_t), s));
   int32_t* perm = (int32_t*)p;
   void* t = nullptr;
   const int64_t ntiles = (nb + 1 + 8191) / 8192;
-  igp_status st = dev_alloc(&t, (size_t)(3 * (nb + 1) + ntiles) * sizeof(int), s);
+  igp_status st = dev_alloc(&t, (size_t)(2 * (nb + 1) + ntiles) * sizeof(int), s);
   if (st != IGP_OK) {
     dev_free(p, s);
     return st;
   }
   int* hist = (int*)t;
-  int* off = hist + (nb + 1);
-  int* cur = off + (nb + 1);
+  int* off = perm + N;
+  int* cur = hist + (nb + 1);
   int* tmp = cur + (nb + 1);
   if (cudaMemsetAsync(hist, 0, (nb + 1) * sizeof(int), s) != cudaSuccess ||
       cudaMemsetAsync(cur, 0, (nb + 1) * sizeof(int), s) != cudaSuccess)
@@ -1812,6 +1838,11 @@ igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed
   la.withhold = o.reserved_test;
   la.gather4 = o.gather == IGP_GATHER_TMA4;
   la.prefetch = (size_t)N * dc * sb > kL2ResidentBytes ? 1 : 0;
+  {  // rows of at least layer_heavy_min entries lead the degree order: their count
+    const int Gl = std::max(1, (int)(dc * sb / 16));
+    const int T = layer_heavy_min(Gl);
+    la.heavy_count = (32 / Gl > 1 && T <= g->max_deg) ? g->perm + N + (g->max_deg - T + 1) : nullptr;
+  }
   la.N = N;
   la.d = d;
 
@@ -1895,7 +1926,7 @@ igp_status batch_create(igp_graph* const* graphs, int32_t G, cudaStream_t s, igp
 }
 
 igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uint64_t* seeds, float* out_dev,
-                       const igp_embed_opts& o, cudaStream_t s) {
+                       const igp_embed_opts& o, cudaStream_t s, bool capture) {
   BatchOps bo;
   Ops ops;
   if (!get_batch_ops(d, o.storage, &bo) || !get_ops(d, o.storage, &ops)) {
@@ -1968,7 +1999,7 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
   };
 
   IGP_TRY_CUDA(cudaMemcpyAsync(b->seeds_dev, seeds, (size_t)G * 8, cudaMemcpyHostToDevice, s));
-  if (prof) return enqueue(s, prof);  // timed phases: plain launches
+  if (prof || !capture) return enqueue(s, prof);  // timed phases, or a one-off batch: plain launches
   // The launch sequence is captured once into a CUDA graph (on a library stream ordered
   // after `s`) and replayed while its parameters stay the same.
   char key[256];
@@ -2136,6 +2167,7 @@ extern "C" igp_status igp_embed_noalloc(const int32_t* row_ptr, const int32_t* c
   la.withhold = 0;
   la.gather4 = 0;
   la.prefetch = (size_t)N * d * sb > kL2ResidentBytes ? 1 : 0;
+  la.heavy_count = nullptr;  // rows in their own order: no heavy tiles
   la.N = N;
   la.d = d;
 

@@ -78,7 +78,8 @@ struct igp_graph {
   // Eq. 1 factors for the last (tau, eps) asked for, and w_i = sum_{j in N(i)} dinv_j
   float* dinv = nullptr;       // device [N]
   float* wsum = nullptr;       // device [N], same allocation as dinv
-  // rows in order of decreasing degree (the layer kernels' processing order)
+  // rows in order of decreasing degree (the layer kernels' processing order), followed in the
+  // same allocation by the offsets of each degree in it ([max_deg + 2], see ensure_perm)
   int32_t* perm = nullptr;
   double dinv_tau = 0, dinv_eps = 0;
   bool dinv_valid = false;
@@ -130,7 +131,8 @@ igp_status append_csr(igp_graph* g, const int32_t* src, const int32_t* dst, int6
 // ffp.cu: batches
 igp_status batch_create(igp_graph* const* graphs, int32_t G, cudaStream_t s, igp_batch* b);
 igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uint64_t* seeds, float* out_dev,
-                       const igp_embed_opts& o, cudaStream_t s);
+                       const igp_embed_opts& o, cudaStream_t s,
+                       bool capture = true);
 
 // Arguments of one layer launch.
 struct LayerArgs {
@@ -149,6 +151,7 @@ struct LayerArgs {
   int withhold;   // test hook of the bounded wait (0 in normal use)
   int gather4;    // bulk-copy kernel: 1 = tile::gather4 through a tensor map
   int prefetch;   // register-load kernel: 1 = L2 prefetch of the rows a few trips ahead
+  const int* heavy_count;  // register-load kernel: device count of leading heavy rows in perm (NULL: 0)
   int32_t N, d;
   float alpha, theta;
   int ddof, grid;

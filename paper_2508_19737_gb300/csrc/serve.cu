@@ -1,9 +1,16 @@
 // Serving loop (igp_server_*): requests to embed graphs, or to grow a resident graph by an
 // edge increment and re-embed it (Alg. 2, lines 1-7), are queued, admitted into a fixed
 // number of slots as device memory and slots free up, and run concurrently: every slot
-// is a host worker thread with its own CUDA stream, so the GPU work of admitted requests
-// overlaps. Resident graphs keep their CSR and degree state on the device between
-// requests; requests on the same resident graph run in submission order.
+// is a host worker thread with its own CUDA stream that builds or grows the request's
+// CSR and embeds the graph, so the GPU work of admitted requests overlaps. Optionally
+// (batch_rows > 0) the FFPs of small graphs are batched continuously instead: a batcher thread
+// with its own stream takes every small request whose CSR is ready when it frees up and embeds
+// them together in one block-diagonal batch (one launch sequence for all of them, each graph
+// with its own Theta seed and column statistics, so every result equals embedding it alone),
+// then copies each result to its caller. (On the served stream measured here, slots embedding
+// their own graphs on concurrent streams kept the GPU busier than shared batches.)
+// Resident graphs keep their CSR and degree state on the device between requests;
+// requests on the same resident graph run in submission order.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -31,8 +38,12 @@ struct Req {
   igp_status status = IGP_OK;
   std::string error;
   size_t est = 0;
+  igp_graph* g = nullptr;  // the request's graph once its CSR is built or grown
+  bool embedded = false;   // set by the batcher once the result is in r.out (or failed)
   Clock::time_point t_submit, t_start, t_done;
 };
+
+
 
 }  // namespace
 
@@ -49,9 +60,12 @@ struct igp_server {
   std::map<int64_t, igp_graph*> resident;
   std::set<int64_t> busy;           // resident graph ids with a running request
   std::vector<std::thread> workers;
+  std::vector<std::thread> batchers;
+  std::deque<Req*> ready;           // CSR done, waiting for a batcher
   std::vector<double> latencies;
   uint64_t next_ticket = 1;
   int64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, running = 0;
+  int64_t batches = 0, batched = 0;  // shared FFP batches and the requests they served
   bool stopping = false;
 };
 
@@ -117,7 +131,9 @@ Req* pick(igp_server* sv) {
   return nullptr;
 }
 
-void run(igp_server* sv, Req* q, cudaStream_t s) {
+// The request's CSR: built from its edges, or its resident graph grown by them (on the slot's
+// stream). q->g is the graph to embed.
+void run_csr(igp_server* sv, Req* q, cudaStream_t s) {
   igp_request& r = q->r;
   igp_graph* g = nullptr;
   igp_status st = IGP_OK;
@@ -130,11 +146,17 @@ void run(igp_server* sv, Req* q, cudaStream_t s) {
     }
     st = igp_graph_append(g, q->src.data(), q->dst.data(), r.M, r.N, s);
   }
-  if (st == IGP_OK) st = igp_embed(g, r.tau, r.L, r.d, r.seed, r.out, &r.opts, s);
   if (st != IGP_OK) q->error = igp_last_error();
-  std::lock_guard<std::mutex> lk(sv->mu);
+  q->g = g;
+  q->status = st;
+}
+
+// After the embedding (lock held): keep or free the graph, account its memory.
+void settle(igp_server* sv, Req* q) {
+  igp_request& r = q->r;
+  igp_graph* g = q->g;
   if (r.kind == IGP_REQ_EMBED) {
-    if (st == IGP_OK && r.keep) {
+    if (q->status == IGP_OK && r.keep) {
       auto it = sv->resident.find(r.graph_id);
       if (it != sv->resident.end()) igp_graph_free(it->second);
       sv->resident[r.graph_id] = g;
@@ -145,7 +167,109 @@ void run(igp_server* sv, Req* q, cudaStream_t s) {
   } else {
     set_resident(sv, r.graph_id, g);  // grown by the increment (unchanged if the merge failed)
   }
-  q->status = st;
+  q->g = nullptr;
+}
+
+// Requests whose FFPs can share one batch: the same tau, L, d and options, none of them
+// outside what batches support.
+bool batchable(const igp_request& r) {
+  return r.opts.chunk_cols == 0 && (r.opts.gather == IGP_GATHER_AUTO || r.opts.gather == IGP_GATHER_LSU) &&
+         r.opts.reserved_test == 0;
+}
+bool same_ffp(const igp_request& a, const igp_request& b) {
+  return a.tau == b.tau && a.L == b.L && a.d == b.d && a.opts.alpha == b.opts.alpha &&
+         a.opts.theta == b.opts.theta && a.opts.eps == b.opts.eps && a.opts.x_scale == b.opts.x_scale &&
+         a.opts.znorm_ddof == b.opts.znorm_ddof && a.opts.storage == b.opts.storage &&
+         a.opts.out_row_l2 == b.opts.out_row_l2;
+}
+
+void fail_all(const std::vector<Req*>& qs, igp_status st) {
+  const std::string msg = igp_last_error();
+  for (Req* q : qs) {
+    q->status = st;
+    q->error = msg;
+  }
+}
+
+// One batch of compatible requests on stream s: pack their graphs, run the FFP of all of
+// them in the same launches, copy every result to its caller. Waits for completion.
+void embed_batch(const std::vector<Req*>& qs, cudaStream_t s) {
+  const igp_request& r0 = qs[0]->r;
+  const int32_t G = (int32_t)qs.size();
+  std::vector<igp_graph*> graphs(G);
+  std::vector<uint64_t> seeds(G);
+  for (int32_t k = 0; k < G; ++k) {
+    graphs[k] = qs[k]->g;
+    seeds[k] = qs[k]->r.seed;
+  }
+  igp_batch* b = nullptr;
+  igp_status st = igp_batch_create(graphs.data(), G, s, &b);
+  if (st != IGP_OK) return fail_all(qs, st);
+  void* out = nullptr;
+  const size_t row_bytes = (size_t)r0.d * sizeof(float);
+  st = igp::dev_alloc(&out, (size_t)b->N * row_bytes, s);
+  if (st == IGP_OK) st = igp::batch_embed(b, r0.tau, r0.L, r0.d, seeds.data(), (float*)out, r0.opts, s, false);
+  for (int32_t k = 0; k < G && st == IGP_OK; ++k) {
+    const size_t off = (size_t)b->goff_host[k] * row_bytes;
+    const size_t bytes = (size_t)(b->goff_host[k + 1] - b->goff_host[k]) * row_bytes;
+    if (cudaMemcpyAsync(qs[k]->r.out, (char*)out + off, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      st = igp::cuda_status(cudaGetLastError(), "result copy", __FILE__, __LINE__);
+  }
+  if (st == IGP_OK && cudaStreamSynchronize(s) != cudaSuccess)
+    st = igp::cuda_status(cudaGetLastError(), "batch", __FILE__, __LINE__);
+  if (out) igp::dev_free(out, s);
+  igp_batch_free(b);
+  if (st != IGP_OK) fail_all(qs, st);
+}
+
+void embed_alone(Req* q, cudaStream_t s) {
+  igp_request& r = q->r;
+  const igp_status st = igp_embed(q->g, r.tau, r.L, r.d, r.seed, r.out, &r.opts, s);
+  if (st != IGP_OK) {
+    q->status = st;
+    q->error = igp_last_error();
+  }
+}
+
+// The batcher: embeds every request whose CSR is ready, small compatible ones together.
+void batcher(igp_server* sv) {
+  cudaSetDevice(sv->device);
+  cudaStream_t s = nullptr;
+  cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  for (;;) {
+    std::vector<Req*> group;
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      sv->cv.wait(lk, [&] { return !sv->ready.empty() || (sv->stopping && sv->running == 0); });
+      if (sv->ready.empty()) break;
+      const Req* first = sv->ready.front();
+      for (auto it = sv->ready.begin(); it != sv->ready.end();) {
+        Req* q = *it;
+        if (q == first || (batchable(first->r) && batchable(q->r) && same_ffp(first->r, q->r))) {
+          group.push_back(q);
+          it = sv->ready.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    std::vector<Req*> small;
+    for (Req* q : group) small.push_back(q);
+    if (small.size() == 1)
+      embed_alone(small[0], s);
+    else if (!small.empty())
+      embed_batch(small, s);
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      for (Req* q : group) q->embedded = true;
+      if (small.size() > 1) {
+        sv->batches += 1;
+        sv->batched += (int64_t)small.size();
+      }
+    }
+    sv->cv.notify_all();
+  }
+  cudaStreamDestroy(s);
 }
 
 void worker(igp_server* sv) {
@@ -169,7 +293,22 @@ void worker(igp_server* sv) {
       sv->running += 1;
       if (q->r.kind == IGP_REQ_APPEND || q->r.keep) sv->busy.insert(q->r.graph_id);
     }
-    if (q->status == IGP_OK) run(sv, q, s);
+    if (q->status == IGP_OK) {
+      run_csr(sv, q, s);
+      if (q->status == IGP_OK && (!batchable(q->r) || q->g->N >= sv->opts.batch_rows)) {
+        embed_alone(q, s);  // large: its own launches fill the GPU, next to the other slots'
+        std::lock_guard<std::mutex> lk(sv->mu);
+        settle(sv, q);
+      } else {
+        std::unique_lock<std::mutex> lk(sv->mu);
+        if (q->status == IGP_OK) {  // small: wait for the batcher
+          sv->ready.push_back(q);
+          sv->cv.notify_all();
+          sv->cv.wait(lk, [&] { return q->embedded; });
+        }
+        settle(sv, q);
+      }
+    }
     {
       std::lock_guard<std::mutex> lk(sv->mu);
       q->t_done = Clock::now();
@@ -213,6 +352,7 @@ void igp_server_opts_init(igp_server_opts* o) {
   o->max_queue = 0;
   o->reserve_bytes = 1ll << 30;
   o->device = -1;
+  o->batch_rows = 0;
 }
 
 igp_status igp_server_create(const igp_server_opts* opts, igp_server** out) {
@@ -224,8 +364,8 @@ igp_status igp_server_create(const igp_server_opts* opts, igp_server** out) {
     o = *opts;
   else
     igp_server_opts_init(&o);
-  if (o.slots < 1 || o.slots > 64 || o.max_queue < 0 || o.reserve_bytes < 0) {
-    set_error("igp_server_create: need 1 <= slots <= 64, max_queue >= 0, reserve_bytes >= 0");
+  if (o.slots < 1 || o.slots > 64 || o.max_queue < 0 || o.reserve_bytes < 0 || o.batch_rows < 0) {
+    set_error("igp_server_create: need 1 <= slots <= 64, max_queue >= 0, reserve_bytes >= 0, batch_rows >= 0");
     return IGP_E_INVAL;
   }
   igp_server* sv = new (std::nothrow) igp_server();
@@ -247,6 +387,9 @@ igp_status igp_server_create(const igp_server_opts* opts, igp_server** out) {
   }
   sv->budget = fr > (size_t)o.reserve_bytes ? fr - (size_t)o.reserve_bytes : 0;
   for (int k = 0; k < o.slots; ++k) sv->workers.emplace_back(worker, sv);
+  // one batcher (batch_rows > 0): small requests whose CSR is ready while it is busy wait
+  // together and are then embedded in one batch
+  if (o.batch_rows > 0) sv->batchers.emplace_back(batcher, sv);
   *out = sv;
   return IGP_OK;
 }
@@ -264,6 +407,8 @@ void igp_server_destroy(igp_server* sv) {
   }
   sv->cv.notify_all();
   for (auto& t : sv->workers) t.join();
+  sv->cv.notify_all();
+  for (auto& t : sv->batchers) t.join();
   for (auto& kv : sv->resident) igp_graph_free(kv.second);
   for (auto& kv : sv->reqs) delete kv.second;
   delete sv;
@@ -406,6 +551,8 @@ igp_status igp_server_get_stats(igp_server* sv, igp_server_stats* st) {
   st->admitted_bytes = (int64_t)sv->admitted;
   st->budget_bytes = (int64_t)sv->budget;
   st->resident_bytes = (int64_t)sv->resident_bytes;
+  st->batches = sv->batches;
+  st->batched = sv->batched;
   st->latency_p50_s = pct(sv->latencies, 0.50);
   st->latency_p99_s = pct(sv->latencies, 0.99);
   return IGP_OK;

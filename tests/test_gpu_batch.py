@@ -1,5 +1,6 @@
-"""Batches (block-diagonal packing of many graphs): every graph's result in the batch is
-bit-identical to igp_embed on that graph alone, and matches the FP64 oracle."""
+"""Batches (block-diagonal packing of many graphs): every graph's result in the batch equals
+igp_embed on that graph alone (to fp32 rounding: igp_embed gathers its highest-degree rows with a
+whole warp, in another summation order) and matches the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -9,6 +10,9 @@ from paper_2508_19737_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 TOL = {"f32": 1e-4, "bf16": 2e-2}
+# two valid fp32 summation orders of the same sums: fp32 agrees to rounding, bf16 storage to
+# the occasional flipped bf16 rounding
+AGREE = {"f32": 1e-5, "bf16": 2e-2}
 
 
 @pytest.fixture(scope="module")
@@ -57,7 +61,7 @@ def test_batch_equals_each_graph_alone(api, d, storage):
         got = out.cpu().numpy()
         for k, (g, (s, t, n)) in enumerate(zip(graphs, edges)):
             alone = api.embed(g, -0.5, 6, d, seeds[k], storage=storage)
-            assert np.array_equal(got[offs[k]:offs[k + 1]], alone), (rep, k)
+            assert _rel(got[offs[k]:offs[k + 1]], alone) <= AGREE[storage], (rep, k)
     # against the oracle on two of the graphs
     for k in (0, 4):
         s, t, n = edges[k]
@@ -71,7 +75,7 @@ def test_batch_equals_each_graph_alone(api, d, storage):
     got = out.cpu().numpy()
     for k in (0, 2, 5):
         alone = api.embed(graphs[k], -0.5, 6, d, seeds2[k], storage=storage)
-        assert np.array_equal(got[offs[k]:offs[k + 1]], alone)
+        assert _rel(got[offs[k]:offs[k + 1]], alone) <= AGREE[storage]
     batch.free()
     for g in graphs:
         g.free()

@@ -164,8 +164,10 @@ def test_chunked_layers_equal_unchunked(api, storage):
         api.embed(gr, -0.5, 8, 64, 5, out=o, storage=storage, chunk_cols=cc)
         outs.append(o.cpu().numpy())
     gr.free()
-    for o in outs[1:]:  # column passes change nothing: the statistics are exact integer sums
-        assert np.array_equal(o, outs[0])
+    # column passes change only the fp32 summation order of the heavy rows (the whole-warp
+    # gather depends on the lanes per row); the statistics are exact integer sums
+    for o in outs[1:]:
+        assert row_rel_err(o, outs[0]) <= {"f32": 1e-5, "bf16": 2e-2}[storage]
     with pytest.raises(api.IgpError):
         api.embed(api.graph_build(g.src, g.dst, g.N), -0.5, 2, 64, 0, chunk_cols=24)
 
@@ -291,8 +293,9 @@ def test_2m_config_full_size(api):
 
 # ---------------------------------------------------------------------------- gather modes
 @pytest.mark.parametrize("d,storage", [(64, "bf16"), (64, "f32"), (32, "bf16"), (128, "bf16"), (16, "f32")])
-def test_gather_modes_agree_bitwise(api, d, storage):
-    """Register-load and bulk-copy gathers add the same rows in the same order."""
+def test_gather_modes_agree(api, d, storage):
+    """The two bulk-copy gathers add the same rows in the same order; the register-load gather
+    agrees with them to fp32 rounding (it gathers the highest-degree rows with a whole warp)."""
     import torch
     g = synth.dcsbm(7001, 12, 22, 2.4, 5, seed=13)
     gr = api.graph_build(g.src, g.dst, g.N)
@@ -303,8 +306,8 @@ def test_gather_modes_agree_bitwise(api, d, storage):
         outs[mode] = o.cpu().numpy()
     gr.sync()
     gr.free()
-    assert np.array_equal(outs["lsu"], outs["bulk"])
-    assert np.array_equal(outs["lsu"], outs["tma4"])
+    assert np.array_equal(outs["bulk"], outs["tma4"])
+    assert row_rel_err(outs["lsu"], outs["bulk"]) <= {"f32": 1e-5, "bf16": 2e-2}[storage]
     rp, col = oracle.build_csr(g.src, g.dst, g.N)
     ref = oracle.ffp(rp, col, oracle.theta_input(9, g.N, d), -0.5, 6)
     assert row_rel_err(outs["lsu"], ref) <= TOL[storage]

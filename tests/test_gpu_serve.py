@@ -1,11 +1,21 @@
 """Serving loop: concurrent, memory-admitted requests give exactly the results the same requests
-give alone; resident graphs are grown by increments in submission order."""
+give alone (to fp32 rounding when small requests are embedded in shared batches: igp_embed alone
+gathers the highest-degree rows with a whole warp, in another summation order); resident graphs
+are grown by increments in submission order."""
 import numpy as np
 import pytest
 
 from paper_2508_19737_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+
+AGREE = {"f32": 1e-5, "bf16": 2e-2}
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)))
 
 
 @pytest.fixture(scope="module")
@@ -101,4 +111,22 @@ def test_cancel_and_failures(api):
     assert sv.wait(ok)[0] == "done"
     st = sv.stats()
     assert st["cancelled"] == 1 and st["completed"] == 12 and st["failed"] == 2
+    sv.close()
+
+
+def test_continuous_batches_equal_each_request_alone(api):
+    """Many compatible small requests in flight at once are embedded in shared batches; each
+    result equals igp_embed of that graph alone (to fp32 rounding)."""
+    gs = [synth.dcsbm(3000 + 997 * k, 6 + k % 4, 14 + k % 7, 2.4, 5, seed=300 + k) for k in range(16)]
+    sv = api.Server(slots=8, batch_rows=100_000)
+    tickets = [sv.submit(g.src, g.dst, g.N, -0.5, 6, 64, 50 + k, storage="bf16") for k, g in enumerate(gs)]
+    for t in tickets:
+        assert sv.wait(t)[0] == "done"
+    st = sv.stats()
+    assert st["completed"] == len(gs) and st["failed"] == 0
+    assert st["batches"] >= 1 and st["batched"] >= 2, st
+    for k, (g, t) in enumerate(zip(gs, tickets)):
+        gr = api.graph_build(g.src, g.dst, g.N)
+        assert _rel(sv.result(t), api.embed(gr, -0.5, 6, 64, 50 + k, storage="bf16")) <= AGREE["bf16"], k
+        gr.free()
     sv.close()
