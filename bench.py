@@ -59,6 +59,23 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The largest x over all ranks (every rank gets it); x itself when world == 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank_step, steps, world, ms):
+    """Whole-job throughput of `world` independent replicas: every rank processes the same units
+    per step, and the job takes the slowest rank's time (ms, max over ranks)."""
+    return units_per_rank_step * steps * world / (ms / 1e3)
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -457,10 +474,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in synth.BATCH_WORKLOADS:
-        return run_batch(args)
-    if args.workload in synth.SERVE_WORKLOADS:
-        return run_serve(args)
+    if args.workload in synth.BATCH_WORKLOADS or args.workload in synth.SERVE_WORKLOADS:
+        if dist_env()[0] != 0:  # one process runs these modes; other ranks have nothing to do
+            return 0
+        return run_batch(args) if args.workload in synth.BATCH_WORKLOADS else run_serve(args)
     import torch
     import torch.distributed as dist
 
@@ -520,16 +537,12 @@ def main():
     barrier()
     launches = api.launch_count() - n0
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
     phases = prof.read()
     prof.close()
     ms_step = ms / args.steps
     units_step = float(nnz) * d * L
-    value = units_step * args.steps * world / (ms / 1e3)
+    value = replica_rate(units_step, args.steps, world, ms)
 
     # end to end through the public API: pinned host edges in, pinned host embeddings out
     src_h = torch.from_numpy(g.src).pin_memory()
@@ -550,12 +563,8 @@ def main():
         step_e2e()
     torch.cuda.synchronize()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = units_step * e2e_steps * world / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = replica_rate(units_step, e2e_steps, world, e2e_s * 1e3)
 
     if rank != 0:
         if world > 1:

@@ -28,6 +28,10 @@ igp_status cuda_status(cudaError_t e, const char* what, const char* file, int li
   return e == cudaErrorMemoryAllocation ? IGP_E_NOMEM : IGP_E_CUDA;
 }
 
+// Kernel launches made by replaying a captured graph of n kernels (capturing counted them
+// once as launches; pass -n to take that back).
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 igp_status after_launch(const char* name) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t e = cudaPeekAtLastError();
@@ -91,6 +95,17 @@ bool is_device_ptr(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device address of page-locked host memory (NULL for any other pointer): kernels write
+// such a buffer directly over the host link, with no staging copy.
+void* pinned_alias(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 int num_sms() {
@@ -407,8 +422,17 @@ igp_status igp_embed(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t se
   const size_t bytes = (size_t)g->N * d * sizeof(float);
   IGP_TRY(graph_wait(g, s));
   igp_status st;
+  void* host_alias = is_device_ptr(out) ? nullptr : pinned_alias(out);
   if (is_device_ptr(out)) {
     st = run_ffp(g, tau, L, d, seed, out, o, s);
+  } else if (host_alias) {  // page-locked host output: written by the output kernel itself
+    st = run_ffp(g, tau, L, d, seed, (float*)host_alias, o, s);
+    if (st == IGP_OK && cudaStreamSynchronize(s) != cudaSuccess)
+      st = cuda_status(cudaGetLastError(), "stream synchronize", __FILE__, __LINE__);
+    if (st == IGP_OK && *g->err_host) {
+      set_error("igp_embed: a device-side wait ran out; the output is invalid");
+      st = IGP_E_TIMEOUT;
+    }
   } else {
     void* tmp = nullptr;
     IGP_TRY(dev_alloc(&tmp, bytes, s));

@@ -172,13 +172,15 @@ __device__ __forceinline__ void theta8(uint64_t seed, uint64_t i, uint64_t q, fl
   }
 }
 
-// Theta, stored as dinv_i * Theta_i when dinv is given (the layer storage convention).
+// Theta, stored as dinv_i * Theta_i when dinv is given (the layer storage convention); thread
+// `tid` of `nthreads` takes work items tid, tid + nthreads, ..
 template <typename S>
-__global__ void k_theta(uint64_t seed, int32_t N, int32_t d, int32_t dc, float xs, const float* __restrict__ dinv,
-                        S* __restrict__ out) {
+__device__ __forceinline__ void theta_part(uint64_t seed, int32_t N, int32_t d, int32_t dc, float xs,
+                                           const float* __restrict__ dinv, S* __restrict__ out, int64_t tid,
+                                           int64_t nthreads) {
   const int nq = d >> 3;
   const int64_t total = (int64_t)N * nq;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t t = tid; t < total; t += nthreads) {
     const int64_t i = t / nq;
     const int q = (int)(t - i * nq);
     float z[8];
@@ -201,16 +203,24 @@ __global__ void k_theta(uint64_t seed, int32_t N, int32_t d, int32_t dc, float x
   }
 }
 
+template <typename S>
+__global__ void k_theta(uint64_t seed, int32_t N, int32_t d, int32_t dc, float xs, const float* __restrict__ dinv,
+                        S* __restrict__ out) {
+  theta_part<S>(seed, N, d, dc, xs, dinv, out, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                (int64_t)gridDim.x * blockDim.x);
+}
+
 // ------------------------------------------------------------------ per-graph helpers
 // w_i = sum_{j in N(i)} dinv_j, fixed order: eight lanes per row, lane s adding entries
 // s, s + 8, s + 16, .. (four index loads, then four gathers, in flight at a time), then an
 // xor tree over the eight lanes. A warp takes four consecutive rows per tile.
-__global__ void k_wsum(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                       const float* __restrict__ dinv, int32_t N, float* __restrict__ wsum) {
+// Warp `wid` of `nwarps` takes tiles wid, wid + nwarps, ..
+__device__ __forceinline__ void wsum_part(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                          const float* __restrict__ dinv, int32_t N, float* __restrict__ wsum,
+                                          int64_t wid, int64_t nwarps) {
   const int sub = threadIdx.x & 7, grp = (threadIdx.x & 31) >> 3;
   const int64_t ntiles = ((int64_t)N + 3) >> 2;
-  for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < ntiles;
-       tile += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+  for (int64_t tile = wid; tile < ntiles; tile += nwarps) {
     const int64_t i = tile * 4 + grp;
     const bool ok = i < N;
     const int b = ok ? row_ptr[i] : 0, e = ok ? row_ptr[i + 1] : 0;
@@ -229,6 +239,27 @@ __global__ void k_wsum(const int32_t* __restrict__ row_ptr, const int32_t* __res
     for (int o = 4; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (ok && sub == 0) wsum[i] = a;
   }
+}
+
+__global__ void k_wsum(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                       const float* __restrict__ dinv, int32_t N, float* __restrict__ wsum) {
+  wsum_part(row_ptr, col, dinv, N, wsum, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+            ((int64_t)gridDim.x * blockDim.x) >> 5);
+}
+
+// Theta and w in one launch: the first half of every CTA's warps draw Theta (arithmetic-bound),
+// the second half sum w (bound by the latency of its gathers), so the two overlap on every SM.
+template <typename S>
+__global__ void __launch_bounds__(256) k_theta_wsum(uint64_t seed, int32_t N, int32_t d, int32_t dc, float xs,
+                                                    const float* __restrict__ dinv, S* __restrict__ out,
+                                                    const int32_t* __restrict__ row_ptr,
+                                                    const int32_t* __restrict__ col, float* __restrict__ wsum) {
+  const int half = blockDim.x >> 1;
+  if ((int)threadIdx.x < half)
+    theta_part<S>(seed, N, d, dc, xs, dinv, out, (int64_t)blockIdx.x * half + threadIdx.x, (int64_t)gridDim.x * half);
+  else
+    wsum_part(row_ptr, col, dinv, N, wsum, ((int64_t)blockIdx.x * half + (threadIdx.x - half)) >> 5,
+              ((int64_t)gridDim.x * half) >> 5);
 }
 
 // Rows in order of decreasing degree (counting sort by key max_deg - deg: block-local
@@ -1688,11 +1719,15 @@ bool get_ops(int d, int storage, Ops* o) {
   }
 }
 
-igp_status launch_dinv_wsum(const int32_t* row_ptr, const int32_t* col, int32_t N, double tau, double eps,
-                            float* dinv, float* wsum, cudaStream_t s) {
+igp_status launch_dinv(const int32_t* row_ptr, int32_t N, double tau, double eps, float* dinv, cudaStream_t s) {
   int blocks = (int)std::min<int64_t>(((int64_t)N + 255) / 256, (int64_t)num_sms() * 8);
   k_dinv<<<std::max(blocks, 1), 256, 0, s>>>(row_ptr, N, tau, eps, dinv);
-  IGP_TRY(after_launch("k_dinv"));
+  return after_launch("k_dinv");
+}
+
+igp_status launch_dinv_wsum(const int32_t* row_ptr, const int32_t* col, int32_t N, double tau, double eps,
+                            float* dinv, float* wsum, cudaStream_t s) {
+  IGP_TRY(launch_dinv(row_ptr, N, tau, eps, dinv, s));
   int wblocks = (int)std::min<int64_t>(((int64_t)N * 8 + 255) / 256, (int64_t)num_sms() * 8);
   k_wsum<<<std::max(wblocks, 1), 256, 0, s>>>(row_ptr, col, dinv, N, wsum);
   return after_launch("k_wsum");
@@ -1760,6 +1795,19 @@ igp_status compute_dinv(igp_graph* g, double tau, double eps, cudaStream_t s, Pr
   return IGP_OK;
 }
 
+// Theta into `out` and, in the same launch, w of the graph (row_ptr, col) from dinv.
+igp_status launch_theta_wsum(uint64_t seed, int32_t N, int32_t d, int32_t dc, float xs, int storage,
+                             const float* dinv, void* out, const int32_t* row_ptr, const int32_t* col, float* wsum,
+                             cudaStream_t s) {
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)N * 8 + 127) / 128, (int64_t)num_sms() * 8));
+  if (storage == IGP_STORE_BF16)
+    k_theta_wsum<__nv_bfloat16><<<blocks, 256, 0, s>>>(seed, N, d, dc, xs, dinv, (__nv_bfloat16*)out, row_ptr, col,
+                                                       wsum);
+  else
+    k_theta_wsum<float><<<blocks, 256, 0, s>>>(seed, N, d, dc, xs, dinv, (float*)out, row_ptr, col, wsum);
+  return after_launch("k_theta_wsum");
+}
+
 igp_status launch_theta(uint64_t seed, int32_t N, int32_t d, int32_t dc, float xs, int storage, const float* dinv,
                         void* out, cudaStream_t s) {
   int64_t total = (int64_t)N * (d / 8);
@@ -1784,7 +1832,19 @@ igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed
     return IGP_E_INVAL;
   }
   const int nchunks = d / dc;
-  IGP_TRY(compute_dinv(g, tau, o.eps, s, prof));
+  // Eq. 1 factors (cached per tau); w comes with Theta below when it has to be recomputed
+  const bool w_ready = g->dinv_valid && g->dinv_tau == tau && g->dinv_eps == o.eps;
+  if (!w_ready) {
+    g->dinv_valid = false;
+    if (!g->dinv) {
+      void* p = nullptr;
+      IGP_TRY(dev_alloc(&p, (size_t)g->N * 2 * sizeof(float), s));
+      g->dinv = (float*)p;
+      g->wsum = g->dinv + g->N;
+    }
+    PhaseTimer pt(prof, IGP_PHASE_DINV, s);
+    IGP_TRY(launch_dinv(g->row_ptr, N, tau, o.eps, g->dinv, s));
+  }
   IGP_TRY(ensure_perm(g, s));
   const bool tma = use_tma(o.gather, dc, sb);
   if (o.gather == IGP_GATHER_TMA4 && dc != d) {
@@ -1820,11 +1880,25 @@ igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed
   {
     PhaseTimer pt(prof, IGP_PHASE_THETA, s);
     if (o.x_in) {
+      if (!w_ready) {
+        const int wblocks = (int)std::min<int64_t>(((int64_t)N * 8 + 255) / 256, (int64_t)num_sms() * 8);
+        k_wsum<<<std::max(wblocks, 1), 256, 0, s>>>(g->row_ptr, g->col, g->dinv, N, g->wsum);
+        IGP_TRY(after_launch("k_wsum"));
+      }
       IGP_TRY(ops.prescale(o.x_in, g->dinv, N, d, dc, T0, s));
     } else {
       const double xs = o.x_scale > 0 ? o.x_scale : 1.0 / std::sqrt((double)d);
-      IGP_TRY(launch_theta(seed, N, d, dc, (float)xs, o.storage, g->dinv, T0, s));
+      if (w_ready)
+        IGP_TRY(launch_theta(seed, N, d, dc, (float)xs, o.storage, g->dinv, T0, s));
+      else
+        IGP_TRY(launch_theta_wsum(seed, N, d, dc, (float)xs, o.storage, g->dinv, T0, g->row_ptr, g->col,
+                                  g->wsum, s));
     }
+  }
+  if (!w_ready) {
+    g->dinv_valid = true;
+    g->dinv_tau = tau;
+    g->dinv_eps = o.eps;
   }
   LayerArgs la;
   la.row_ptr = g->row_ptr;
@@ -2016,9 +2090,12 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
       b->exec = nullptr;
     }
     cudaGraph_t graph = nullptr;
+    const int64_t n0 = igp_launch_count();
     IGP_TRY_CUDA(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
     igp_status st = enqueue(b->cs, nullptr);
     cudaError_t e = cudaStreamEndCapture(b->cs, &graph);
+    b->exec_kernels = igp_launch_count() - n0;
+    count_launches(-b->exec_kernels);  // captured, not run: counted when the graph runs
     if (st != IGP_OK) {
       if (graph) cudaGraphDestroy(graph);
       return st;
@@ -2030,6 +2107,7 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
     b->exec_key = key;
   }
   IGP_TRY_CUDA(cudaGraphLaunch(b->exec, b->cs));
+  count_launches(b->exec_kernels);
   IGP_TRY_CUDA(cudaEventRecord(b->ev_out, b->cs));
   IGP_TRY_CUDA(cudaStreamWaitEvent(s, b->ev_out, 0));
   return IGP_OK;

@@ -32,6 +32,8 @@ igp_status cuda_status(cudaError_t e, const char* what, const char* file, int li
 
 // Count one kernel launch and surface launch-configuration errors.
 igp_status after_launch(const char* name);
+// Add n to the launch count (the kernels of a replayed graph; negative to take back captured ones).
+void count_launches(int64_t n);
 
 // ---------------------------------------------------------------- memory
 // Stream-ordered allocation from a library-private pool that keeps freed memory
@@ -116,6 +118,7 @@ struct igp_batch {
   cudaStream_t cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t exec = nullptr;
+  int64_t exec_kernels = 0;  // kernels in exec
   std::string exec_key;
 };
 

@@ -56,8 +56,11 @@ def test_batch_equals_each_graph_alone(api, d, storage):
     out = torch.empty((N, d), dtype=torch.float32, device="cuda")
     for rep in range(2):  # second call replays the captured launch sequence
         out.fill_(-1.0)
+        n0 = api.launch_count()
         batch.embed(-0.5, 6, d, seeds, out=out, storage=storage)
         torch.cuda.synchronize()
+        # theta, 6 x (layer + statistics), output: counted whether launched or replayed
+        assert api.launch_count() - n0 >= 1 + 6 * 2 + 1
         got = out.cpu().numpy()
         for k, (g, (s, t, n)) in enumerate(zip(graphs, edges)):
             alone = api.embed(g, -0.5, 6, d, seeds[k], storage=storage)

@@ -219,6 +219,24 @@ def test_host_output_and_x_in(api):
     assert row_rel_err(out, oracle.ffp(rp, col, Xc.astype(np.float64), -0.5, 5)) <= TOL["f32"]
 
 
+def test_pinned_host_output_equals_device_output(api):
+    """A page-locked host output is written by the output kernel directly; the result is the
+    device-output result, bit for bit (pageable outputs are staged through the device)."""
+    import torch
+    g = synth.dcsbm(30011, 20, 24, 2.4, 5, seed=12)
+    gr = api.graph_build(g.src, g.dst, g.N)
+    for storage in ("f32", "bf16"):
+        dev = torch.empty((g.N, 64), dtype=torch.float32, device="cuda")
+        api.embed(gr, -0.5, 6, 64, 4, out=dev, storage=storage)
+        pinned = torch.full((g.N, 64), -1.0, dtype=torch.float32).pin_memory()
+        api.embed(gr, -0.5, 6, 64, 4, out=pinned, storage=storage)
+        pageable = np.full((g.N, 64), -1.0, dtype=np.float32)
+        api.embed(gr, -0.5, 6, 64, 4, out=pageable, storage=storage)
+        d = dev.cpu().numpy()
+        assert np.array_equal(pinned.numpy(), d) and np.array_equal(pageable, d)
+    gr.free()
+
+
 def test_bf16_against_bf16_emulating_oracle(api):
     g = synth.dcsbm(20011, 32, 25, 2.5, 4, seed=7, dirichlet_alpha=2.0)
     got, ref, (rp, col, X, _) = _ffp_case(api, g.src, g.dst, g.N, 64, -0.5, 10, storage="bf16")
