@@ -308,8 +308,8 @@ igp_status igp_server_get_stats(igp_server* sv, igp_server_stats* stats);
  *   tau, L, d, seed, opts : as for igp_embed; opts->profile and opts->chunk_cols must be 0
  * Same result as igp_embed on the graph built from that CSR. All temporaries live in a fixed
  * 16 MiB device array inside the library, reserved on every GPU that loads the library until the
- * process exits; sizes whose temporaries do not fit (about 2 N d storage-size bytes plus 12 N bytes
- * and the column-statistics partials) are rejected with IGP_E_INVAL before any GPU work. The call
+ * process exits; sizes whose temporaries do not fit (about 2 N d storage-size bytes plus 8 N bytes
+ * and 32 d bytes of column statistics) are rejected with IGP_E_INVAL before any GPU work. The call
  * issues no cudaMalloc, cudaFree or other allocating routine. The first call on each device looks
  * up that device's address of the array (cudaGetSymbolAddress); make it before any stream capture.
  * All calls share the array: calls whose GPU work overlaps (other streams, other threads) race, so
