@@ -379,6 +379,9 @@ constexpr int kBucketThreads = 1024;   // k_bucket_rows
 constexpr int kBucketCap = 52 * 1024;  // entries a bucket places in shared memory (208 KB)
 constexpr int kMaxLocalRows = 1024;    // rows per bucket
 constexpr int kRegSortMax = 512;       // longest row a warp sorts in registers
+constexpr int kGroupWarps = 4;         // warps of a group that sorts one longer row in shared memory
+constexpr int kGroupSortMax = 8192;    // longest row a group sorts (longer ones: the whole CTA)
+constexpr int kMaxLongRows = 512;      // longer rows of a bucket listed for the groups
 constexpr int kLoadBatch = 8;          // independent loads a thread issues before using them
 
 struct PartGeom {
@@ -464,6 +467,16 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __
   const int64_t e1 = e0 + per < M ? e0 + per : M;
   constexpr int BPT = (1 << kPartMaxBits) / kPartThreads;  // buckets per thread in the scan
   for (int64_t t0 = e0; t0 < e1; t0 += kPartTile) {
+    {  // the next round's edges into L2, read after this round: kPartTile ids of each array are
+       // kPartTile / 32 lines of 128 bytes; one line per thread
+      constexpr int kLines = kPartTile / 32;
+      const int64_t n0 = t0 + kPartTile;
+      if ((int)threadIdx.x < 2 * kLines) {
+        const int64_t at = n0 + (int64_t)(threadIdx.x % kLines) * 32;
+        const int32_t* arr = (int)threadIdx.x < kLines ? src : dst;
+        if (at < e1) asm volatile("prefetch.global.L2 [%0];" ::"l"(arr + at));
+      }
+    }
     for (int b = threadIdx.x; b < NB; b += blockDim.x) s_cnt[b] = 0;
     __syncthreads();
     int32_t eu[EPT], ev[EPT];  // this thread's edges of the round (eu = -1: none)
@@ -590,6 +603,57 @@ __device__ __forceinline__ int warp_sort_unique_any(const int32_t* src, int n, i
   return warp_sort_unique<16>(src, n, out);
 }
 
+// One warp: write the distinct values of the sorted w[0..n) to out (which may be w), ascending;
+// returns their count.
+__device__ int warp_unique_sorted(const int32_t* w, int n, int32_t* out) {
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  int32_t carry = INT_MIN;  // last value of the previous chunk, read before any write
+  for (int c = 0; c < n; c += 32) {
+    const int t = c + lane;
+    const int32_t v = t < n ? w[t] : 0;
+    int32_t prev = __shfl_up_sync(0xffffffffu, v, 1);
+    if (lane == 0) prev = carry;
+    const bool f = t < n && v != prev;
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    carry = __shfl_sync(0xffffffffu, v, 31);
+    __syncwarp();  // the chunk is read before it is overwritten
+    if (f) out[base + __popc(m & lanemask_lt())] = v;
+    base += __popc(m);
+    __syncwarp();
+  }
+  return base;
+}
+
+// Barrier of the kGroupWarps warps of group `id` (named barrier id + 1; 0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id + 1), "r"(kGroupWarps * 32) : "memory");
+}
+
+// The warps of one group: bitonic sort of a[0..n) in shared memory (the network of
+// block_bitonic, comparators spread over the group's threads).
+__device__ void group_bitonic(int32_t* a, int n, int gtid, int gid) {
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int k = 2; k <= P; k <<= 1) {
+    const int h = k >> 1;
+    for (int t = gtid; t < (P >> 1); t += kGroupWarps * 32) {
+      int i = ((t & ~(h - 1)) << 1) | (t & (h - 1));
+      int p = i ^ (k - 1);
+      if (p < n) cswap(a, i, p);
+    }
+    group_sync(gid);
+    for (int j = k >> 2; j >= 1; j >>= 1) {
+      for (int t = gtid; t < (P >> 1); t += kGroupWarps * 32) {
+        int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+        int p = i + j;
+        if (p < n) cswap(a, i, p);
+      }
+      group_sync(gid);
+    }
+  }
+}
+
 // Whole CTA: sort a[0..n) in place (shared or global memory), then write the distinct
 // values, ascending, to out (which may be a). Returns the distinct count (all threads).
 __device__ int block_sort_unique(int32_t* a, int n, int32_t* out, int* warp_tot, int* total, int32_t* carry_last) {
@@ -628,6 +692,8 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket_rows(uint32_t* __rest
   __shared__ int total;
   __shared__ int32_t carry_last;
   __shared__ int s_max;
+  __shared__ int s_long[kMaxLongRows];
+  __shared__ int s_nlong;
   const int b = blockIdx.x;
   const int NB = 1 << kb;
   if (b >= N) return;  // no rows
@@ -639,7 +705,10 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket_rows(uint32_t* __rest
   uint32_t* ent = ebuf + e0;
   int32_t* place = fits ? s_col : obuf + e0;
   for (int r = threadIdx.x; r < kMaxLocalRows; r += blockDim.x) s_cnt[r] = 0;
-  if (threadIdx.x == 0) s_max = 0;
+  if (threadIdx.x == 0) {
+    s_max = 0;
+    s_nlong = 0;
+  }
   __syncthreads();
   for (int k0 = threadIdx.x; k0 < E; k0 += kLoadBatch * blockDim.x) {
     uint32_t x[kLoadBatch];
@@ -672,23 +741,55 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket_rows(uint32_t* __rest
   }
   __syncthreads();
   // sort + distinct in place; s_cur[r] := distinct count of row r. Warps take rows up to
-  // kRegSortMax entries (in registers); the whole CTA takes longer rows afterwards, one at
-  // a time, in shared memory (a bucket placed in global memory lends its unused shared
-  // buffer for that).
+  // kRegSortMax entries (in registers); groups of kGroupWarps warps then take the longer
+  // rows up to kGroupSortMax entries of a bucket placed in shared memory, one row per group
+  // at a time; the whole CTA takes what is left, one row at a time, in shared memory (a
+  // bucket placed in global memory lends its unused shared buffer for that).
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int gmax = fits ? kGroupSortMax : kRegSortMax;  // longest row the groups take
   int local_max = 0;
   for (int r = warp; r < R; r += nwarps) {
     const int n = s_cnt[r];
-    if (n > kRegSortMax) continue;  // below, by the whole CTA
+    if (n > kRegSortMax) {  // below
+      if (lane == 0 && n <= gmax) {
+        const int k = atomicAdd(&s_nlong, 1);
+        if (k < kMaxLongRows) s_long[k] = r;
+      }
+      continue;
+    }
     const int uq = n > 0 ? warp_sort_unique_any(place + s_off[r], n, place + s_off[r]) : 0;
     if (lane == 0) s_cur[r] = uq;
     local_max = max(local_max, uq);
   }
   if (lane == 0 && local_max > 0) atomicMax(&s_max, local_max);
   __syncthreads();
+  {
+    const int nlong = min(s_nlong, kMaxLongRows);
+    const int gid = warp / kGroupWarps, gtid = threadIdx.x - gid * kGroupWarps * 32;
+    const int ngroups = nwarps / kGroupWarps;
+    for (int k = gid; k < nlong; k += ngroups) {
+      const int r = s_long[k];
+      int32_t* a = place + s_off[r];
+      group_bitonic(a, s_cnt[r], gtid, gid);
+      if (gtid < 32) {
+        const int uq = warp_unique_sorted(a, s_cnt[r], a);
+        if (lane == 0) {
+          s_cur[r] = uq;
+          atomicMax(&s_max, uq);
+        }
+      }
+      group_sync(gid);
+    }
+  }
+  __syncthreads();
   for (int r = 0; r < R; ++r) {
     const int n = s_cnt[r];
     if (n <= kRegSortMax) continue;
+    if (n <= gmax) {  // done by a group, unless the list was full
+      bool listed = false;
+      for (int k = 0; k < min(s_nlong, kMaxLongRows) && !listed; ++k) listed = s_long[k] == r;
+      if (listed) continue;
+    }
     int32_t* a = place + s_off[r];
     int uq;
     if (!fits && n <= kBucketCap) {  // global placement: sort a copy in shared memory
