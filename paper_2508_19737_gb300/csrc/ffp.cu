@@ -1143,7 +1143,9 @@ __global__ void k_output(const S* __restrict__ T, const float* __restrict__ dinv
 // The processing order lists each graph's rows by decreasing degree, padded with -1 to
 // a multiple of kBatchAlign, so a warp tile never mixes graphs.
 constexpr int kBatchAlign = 32;
-constexpr int kBatchChunk = 64;  // order positions per warp turn (a multiple of kBatchAlign)
+// Order positions per warp turn (a multiple of kBatchAlign), tried on the first embedding of a
+// batch at each (d, storage); the fastest is kept.
+constexpr int kBatchChunks[] = {32, 64, 128, 256};
 
 struct PackSrc {
   const int32_t* row_ptr;  // graph's own CSR
@@ -1203,7 +1205,7 @@ __global__ void k_theta_batch(const uint64_t* __restrict__ seeds, const int32_t*
 }
 
 // One Eq. 4 layer over a batch: the gather/epilogue of k_layer. The processing order is
-// cut into chunks of kBatchChunk positions that warps claim in order from a global
+// cut into chunks of `chunk` positions that warps claim in order from a global
 // counter, so at any time the GPU works on a narrow window of the order, i.e. on a few
 // graphs, whose rows (the only ones their neighbours can be) stay in L2; claiming also
 // balances the load. (Which warp takes which rows changes nothing in the result.) The column statistics are kept per graph
@@ -1214,7 +1216,7 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer_bat
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const float* __restrict__ dinv,
     const float* __restrict__ wsum, const int32_t* __restrict__ perm, const int32_t* __restrict__ pgraph, int64_t P,
     const S* __restrict__ Tin, S* __restrict__ Tout_all, const float* __restrict__ stats_in,
-    unsigned long long* __restrict__ gsum, unsigned* __restrict__ chunk_ctr, float alpha, float theta) {
+    unsigned long long* __restrict__ gsum, unsigned* __restrict__ chunk_ctr, float alpha, float theta, int chunk) {
   using RW = Raw<S>;
   using RT = typename RW::T;
   constexpr int VPL = Store<S>::VPL;
@@ -1233,12 +1235,12 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer_bat
   auto claim = [&]() -> int64_t {
     unsigned c = 0;
     if (lane == 0) c = atomicAdd(chunk_ctr, 1u);
-    return (int64_t)__shfl_sync(0xffffffffu, c, 0) * kBatchChunk;
+    return (int64_t)__shfl_sync(0xffffffffu, c, 0) * chunk;
   };
   int64_t next_chunk = claim();
   auto next_pos = [&](int64_t p) -> int64_t {
     const int64_t q = p + GPW;
-    if (q % kBatchChunk) return q;
+    if (q % chunk) return q;
     const int64_t c = next_chunk;
     next_chunk = claim();
     return c;
@@ -1607,10 +1609,12 @@ struct BatchCfg {
 
 template <int D, typename S>
 igp_status batch_layer_launch(const igp_batch* b, const void* Tin, void* Tout, const float* st_in,
-                              unsigned long long* gsum, float alpha, float theta, int grid, cudaStream_t s) {
+                              unsigned long long* gsum, float alpha, float theta, int grid, int chunk,
+                              cudaStream_t s) {
   k_layer_batch<D, S><<<grid, kLayerThreads, 0, s>>>(b->row_ptr, b->col, b->dinv, b->wsum, b->perm, b->pgraph,
                                                      b->P, (const S*)Tin, (S*)Tout, st_in, gsum,
-                                                     (unsigned*)(gsum + (int64_t)b->G * 2 * D), alpha, theta);
+                                                     (unsigned*)(gsum + (int64_t)b->G * 2 * D), alpha, theta,
+                                                     chunk);
   return after_launch("k_layer_batch");
 }
 
@@ -1646,7 +1650,7 @@ igp_status batch_theta_launch(const igp_batch* b, int d, float xs, void* out, cu
 struct BatchOps {
   int (*per_sm)();
   igp_status (*layer)(const igp_batch*, const void*, void*, const float*, unsigned long long*, float, float, int,
-                      cudaStream_t);
+                      int, cudaStream_t);
   igp_status (*tail)(const igp_batch*, unsigned long long*, int, float*, cudaStream_t);
   igp_status (*output)(const igp_batch*, const void*, const float*, int, float*, cudaStream_t);
   igp_status (*theta)(const igp_batch*, int, float, void*, cudaStream_t);
@@ -2025,9 +2029,11 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
     b->dinv_eps = o.eps;
     b->exec_key.clear();
   }
-  // one full wave of CTAs, each warp taking chunks of the order grid-stride
-  const int64_t want = (b->P + kLayerWarps * kBatchChunk - 1) / (kLayerWarps * kBatchChunk);
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)bo.per_sm() * num_sms()));
+  // one full wave of CTAs (fewer for a short order), warps claiming chunks of the order
+  auto grid_for = [&](int chunk) {
+    const int64_t want = (b->P + (int64_t)kLayerWarps * chunk - 1) / ((int64_t)kLayerWarps * chunk);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)bo.per_sm() * num_sms()));
+  };
   // workspace: T0 | T1 | stats[2][G][2d] | gsum[G][2d]
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t bT = al((size_t)N * d * sb);
@@ -2051,6 +2057,46 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
   unsigned long long* gsum = (unsigned long long*)(base + 2 * bT + bS);
   const double xs = o.x_scale > 0 ? o.x_scale : 1.0 / std::sqrt((double)d);
 
+  IGP_TRY_CUDA(cudaMemcpyAsync(b->seeds_dev, seeds, (size_t)G * 8, cudaMemcpyHostToDevice, s));
+  // Schedule tuning: on the first embedding at this (d, storage), one layer is timed for each
+  // claim size (each followed by the statistics kernel, which clears what the layer added);
+  // the fastest is kept for the batch.
+  const int tkey = d * 2 + o.storage;
+  if (!b->tuned_chunk.count(tkey)) {
+    const int nc = (int)(sizeof(kBatchChunks) / sizeof(kBatchChunks[0]));
+    cudaEvent_t ev[2 * 4];
+    for (int k = 0; k < 2 * nc; ++k) IGP_TRY_CUDA(cudaEventCreate(&ev[k]));
+    igp_status st = IGP_OK;
+    if (cudaMemsetAsync(gsum, 0, bQ, s) != cudaSuccess) st = cuda_status(cudaGetLastError(), "memset", __FILE__, __LINE__);
+    if (st == IGP_OK) st = bo.theta(b, d, (float)xs, T0, s);
+    for (int k = 0; k < nc && st == IGP_OK; ++k) {
+      cudaEventRecord(ev[2 * k], s);
+      st = bo.layer(b, T0, T1, nullptr, gsum, (float)o.alpha, (float)o.theta, grid_for(kBatchChunks[k]),
+                    kBatchChunks[k], s);
+      cudaEventRecord(ev[2 * k + 1], s);
+      if (st == IGP_OK) st = bo.tail(b, gsum, o.znorm_ddof, stats, s);
+    }
+    int best = kBatchChunks[1];
+    float best_ms = 1e30f;
+    for (int k = 0; k < nc && st == IGP_OK; ++k) {
+      float ms = 0.0f;
+      if (cudaEventSynchronize(ev[2 * k + 1]) != cudaSuccess || cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]) != cudaSuccess) {
+        st = cuda_status(cudaGetLastError(), "schedule tuning", __FILE__, __LINE__);
+        break;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = kBatchChunks[k];
+      }
+    }
+    for (int k = 0; k < 2 * nc; ++k) cudaEventDestroy(ev[k]);
+    IGP_TRY(st);
+    b->tuned_chunk[tkey] = best;
+    b->exec_key.clear();
+  }
+  const int chunk = b->tuned_chunk[tkey];
+  const int grid = grid_for(chunk);
+
   auto enqueue = [&](cudaStream_t q, Profile* pf) -> igp_status {
     IGP_TRY_CUDA(cudaMemsetAsync(gsum, 0, bQ, q));
     {
@@ -2063,7 +2109,7 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
       void* dst = (cur == T0) ? T1 : T0;
       float* st = stats + (size_t)(l & 1) * G * 2 * d;
       PhaseTimer pt(pf, IGP_PHASE_LAYER, q);
-      IGP_TRY(bo.layer(b, cur, dst, st_prev, gsum, (float)o.alpha, (float)o.theta, grid, q));
+      IGP_TRY(bo.layer(b, cur, dst, st_prev, gsum, (float)o.alpha, (float)o.theta, grid, chunk, q));
       IGP_TRY(bo.tail(b, gsum, o.znorm_ddof, st, q));
       cur = dst;
       st_prev = st;
@@ -2072,13 +2118,12 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
     return bo.output(b, cur, st_prev, o.out_row_l2, out_dev, q);
   };
 
-  IGP_TRY_CUDA(cudaMemcpyAsync(b->seeds_dev, seeds, (size_t)G * 8, cudaMemcpyHostToDevice, s));
   if (prof || !capture) return enqueue(s, prof);  // timed phases, or a one-off batch: plain launches
   // The launch sequence is captured once into a CUDA graph (on a library stream ordered
   // after `s`) and replayed while its parameters stay the same.
   char key[256];
-  snprintf(key, sizeof(key), "%a|%d|%d|%d|%a|%a|%a|%d|%d|%a|%p|%p", tau, L, d, o.storage, o.alpha, o.theta, o.eps,
-           o.znorm_ddof, o.out_row_l2, xs, (void*)out_dev, b->ws);
+  snprintf(key, sizeof(key), "%a|%d|%d|%d|%a|%a|%a|%d|%d|%a|%p|%p|%d", tau, L, d, o.storage, o.alpha, o.theta,
+           o.eps, o.znorm_ddof, o.out_row_l2, xs, (void*)out_dev, b->ws, chunk);
   if (!b->cs) IGP_TRY_CUDA(cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking));
   if (!b->ev_in) IGP_TRY_CUDA(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
   if (!b->ev_out) IGP_TRY_CUDA(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -119,6 +120,7 @@ struct igp_batch {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t exec_kernels = 0;  // kernels in exec
+  std::map<int, int> tuned_chunk;  // claim size of the batch layer per (d, storage), timed on first use
   std::string exec_key;
 };
 
