@@ -91,6 +91,12 @@ typedef struct igp_embed_opts {
                           width, so passes change results only by fp32 rounding. */
   int32_t gather;      /* IGP_GATHER_AUTO (default), _LSU, _BULK or _TMA4 */
   int32_t reserved_test;/* 0. (Non-zero only in the library's own test of its bounded device waits.) */
+  int32_t out_row_begin;/* first output row, 0 (default) .. N: the call writes rows out_row_begin .. N-1
+                           of Z~ (out row 0 = graph row out_row_begin), so `out` holds (N - out_row_begin)
+                           x d values. After igp_graph_append grew the graph from N_old nodes, N_old
+                           extracts the new nodes' rows (Alg. 2 l.8). The FFP and its statistics still
+                           run over all N rows. With N (no rows) `out` may be NULL and the call is
+                           stream-ordered as for a device output. igp_batch_embed takes only 0. */
   const void* x_in;    /* NULL: Theta from `seed`. Else a DEVICE pointer to N x d row-major values in
                           the storage type, used as Z^(0) instead (not modified). */
   igp_profile* profile;/* NULL, or a profile that records per-phase device times of this call */

@@ -61,6 +61,7 @@ class EmbedOpts(ctypes.Structure):
         ("chunk_cols", ctypes.c_int32),
         ("gather", ctypes.c_int32),
         ("reserved_test", ctypes.c_int32),
+        ("out_row_begin", ctypes.c_int32),
         ("x_in", ctypes.c_void_p),
         ("profile", ctypes.c_void_p),
     ]
@@ -203,7 +204,7 @@ def launch_count():
 
 
 def embed_opts(alpha=1.0, theta=0.1, eps=1e-3, x_scale=0.0, znorm_ddof=1, storage="f32", out_row_l2=False,
-               x_in=None, profile=None, chunk_cols=0, gather="auto", reserved_test=0):
+               x_in=None, profile=None, chunk_cols=0, gather="auto", reserved_test=0, out_row_begin=0):
     o = EmbedOpts()
     lib().igp_embed_opts_init(ctypes.byref(o))
     o.alpha, o.theta, o.eps, o.x_scale = alpha, theta, eps, x_scale
@@ -213,6 +214,7 @@ def embed_opts(alpha=1.0, theta=0.1, eps=1e-3, x_scale=0.0, znorm_ddof=1, storag
     o.chunk_cols = int(chunk_cols)
     o.gather = GATHER[gather] if isinstance(gather, str) else int(gather)
     o.reserved_test = int(reserved_test)
+    o.out_row_begin = int(out_row_begin)
     o.x_in = _ptr(x_in)
     o.profile = profile.handle if profile is not None else None
     return o
@@ -334,13 +336,14 @@ def generate_x(seed, N, d, x_scale=0.0, out=None, stream=None):
 
 
 def embed(g, tau, L, d, seed, out=None, opts=None, stream=None, **kw):
-    """igp_embed: one FFP; returns `out` (a new numpy array if not given)."""
+    """igp_embed: one FFP; returns `out` (a new numpy array if not given) holding rows
+    out_row_begin .. N-1 of the embedding (all rows by default)."""
     if opts is None:
         opts = embed_opts(**kw)
     elif kw:
         raise ValueError("give either opts or keyword options")
     if out is None:
-        out = np.empty((g.N, d), dtype=np.float32)
+        out = np.empty((max(g.N - opts.out_row_begin, 0), d), dtype=np.float32)
     _check(lib().igp_embed(g.handle, float(tau), int(L), int(d), int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out),
                            ctypes.byref(opts), _stream(stream)))
     return out
@@ -419,11 +422,11 @@ class Server:
 
     def submit(self, src, dst, N, tau, L, d, seed, kind="embed", graph_id=0, keep=False, out=None, **kw):
         """Queue a request (host int32 edge arrays, copied now); returns its ticket. The result lands in
-        `out` (a new float32 N x d array unless given), available from result() once done."""
+        `out` (a new float32 (N - out_row_begin) x d array unless given), available from result() once done."""
         src = np.ascontiguousarray(src, dtype=np.int32)
         dst = np.ascontiguousarray(dst, dtype=np.int32)
         if out is None:
-            out = np.empty((N, d), dtype=np.float32)
+            out = np.empty((max(int(N) - int(kw.get("out_row_begin", 0)), 0), d), dtype=np.float32)
         r = Request()
         r.kind = IGP_REQ_EMBED if kind == "embed" else IGP_REQ_APPEND
         r.keep = 1 if keep else 0

@@ -196,6 +196,7 @@ void igp_embed_opts_init(igp_embed_opts* o) {
   o->znorm_ddof = 1;
   o->storage = IGP_STORE_F32;
   o->out_row_l2 = 0;
+  o->out_row_begin = 0;
   o->x_in = nullptr;
   o->profile = nullptr;
 }
@@ -287,11 +288,16 @@ igp_status igp_graph_info(const igp_graph* g, int32_t* N, int64_t* nnz, int32_t*
   return IGP_OK;
 }
 
+// Copies `bytes` from the device to `dst` (host or device); a host destination (also with
+// bytes == 0) returns after the stream has drained, so host-visible results of it are final.
 static igp_status copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
-  if (!dst || bytes == 0) return IGP_OK;
+  if (!dst) return IGP_OK;
   bool dev = is_device_ptr(dst);
-  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return cuda_status(e, "copy out", __FILE__, __LINE__);
+  cudaError_t e = cudaSuccess;
+  if (bytes > 0) {
+    e = cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_status(e, "copy out", __FILE__, __LINE__);
+  }
   if (!dev) {
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_status(e, "stream synchronize", __FILE__, __LINE__);
@@ -388,7 +394,7 @@ igp_status igp_embed(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t se
     o = *opts;
   else
     igp_embed_opts_init(&o);
-  if (!g || !out) {
+  if (!g || (!out && o.out_row_begin != g->N)) {
     set_error("igp_embed: NULL graph or output");
     return IGP_E_INVAL;
   }
@@ -418,13 +424,18 @@ igp_status igp_embed(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t se
     set_error("igp_embed: opts->x_in must be device memory");
     return IGP_E_INVAL;
   }
+  if (o.out_row_begin < 0 || o.out_row_begin > g->N) {
+    set_error("igp_embed: opts->out_row_begin=%d outside [0, N=%d]", o.out_row_begin, g->N);
+    return IGP_E_INVAL;
+  }
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = (size_t)g->N * d * sizeof(float);
+  const size_t bytes = (size_t)(g->N - o.out_row_begin) * d * sizeof(float);
   IGP_TRY(graph_wait(g, s));
   igp_status st;
-  void* host_alias = is_device_ptr(out) ? nullptr : pinned_alias(out);
-  if (is_device_ptr(out)) {
-    st = run_ffp(g, tau, L, d, seed, out, o, s);
+  const bool on_device = bytes == 0 || is_device_ptr(out);  // no rows to write: stream-ordered too
+  void* host_alias = on_device ? nullptr : pinned_alias(out);
+  if (on_device) {
+    st = run_ffp(g, tau, L, d, seed, bytes ? out : nullptr, o, s);
   } else if (host_alias) {  // page-locked host output: written by the output kernel itself
     st = run_ffp(g, tau, L, d, seed, (float*)host_alias, o, s);
     if (st == IGP_OK && cudaStreamSynchronize(s) != cudaSuccess)
@@ -524,8 +535,8 @@ igp_status igp_batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const
     return IGP_E_INVAL;
   }
   if (o.x_in || o.chunk_cols != 0 || (o.gather != IGP_GATHER_AUTO && o.gather != IGP_GATHER_LSU) ||
-      o.reserved_test) {
-    set_error("igp_batch_embed: x_in, chunk_cols, TMA gathers are not supported for batches");
+      o.reserved_test || o.out_row_begin != 0) {
+    set_error("igp_batch_embed: x_in, chunk_cols, TMA gathers and out_row_begin are not supported for batches");
     return IGP_E_INVAL;
   }
   if (d != 8 && d != 16 && d != 32 && d != 64 && d != 128) {

@@ -1089,7 +1089,7 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer_tma(
 // ------------------------------------------------------------------ output
 template <int D, typename S>
 __global__ void k_output(const S* __restrict__ T, const float* __restrict__ dinv, const float* __restrict__ stats,
-                         int32_t N, int32_t dc, int row_l2, float* __restrict__ out) {
+                         int32_t row0, int32_t N, int32_t dc, int row_l2, float* __restrict__ out) {
   constexpr int VPL = Store<S>::VPL;
   constexpr int G = D / VPL;  // lanes per row
   constexpr int RPW = 32 / G;  // rows per warp pass
@@ -1097,7 +1097,8 @@ __global__ void k_output(const S* __restrict__ T, const float* __restrict__ dinv
   const int chunk = lane % G, sub = lane / G;
   const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp_id * RPW; base < N; base += nw * RPW) {  // warp-uniform loop
+  // rows row0 .. N-1 (Alg. 2 l.8 extracts the newest nodes' rows); out row 0 is row row0
+  for (int64_t base = row0 + warp_id * RPW; base < N; base += nw * RPW) {  // warp-uniform loop
     const int64_t i = base + sub;
     const bool ok = i < N;
     float v[VPL];
@@ -1128,7 +1129,7 @@ __global__ void k_output(const S* __restrict__ T, const float* __restrict__ dinv
       for (int e = 0; e < VPL; ++e) o[e] *= inv;
     }
     if (ok) {
-      float* p = out + i * D + chunk * VPL;
+      float* p = out + (i - row0) * D + chunk * VPL;
 #pragma unroll
       for (int e = 0; e < VPL; e += 4)
         *reinterpret_cast<float4*>(p + e) = make_float4(o[e], o[e + 1], o[e + 2], o[e + 3]);
@@ -1576,12 +1577,13 @@ igp_status layer_tma_launch(const LayerArgs& a, cudaStream_t s) {
 }
 
 template <int D, typename S>
-igp_status output_launch(const void* T, const float* dinv, const float* st, int32_t N, int dc, int row_l2, float* out,
-                         cudaStream_t s) {
+igp_status output_launch(const void* T, const float* dinv, const float* st, int32_t row0, int32_t N, int dc,
+                         int row_l2, float* out, cudaStream_t s) {
+  if (row0 >= N) return IGP_OK;  // no rows to write
   constexpr int G = D / Store<S>::VPL;
-  int64_t threads = (int64_t)N * G;
+  int64_t threads = (int64_t)(N - row0) * G;
   int blocks = (int)std::min<int64_t>((threads + 255) / 256, (int64_t)num_sms() * 16);
-  k_output<D, S><<<std::max(blocks, 1), 256, 0, s>>>((const S*)T, dinv, st, N, dc, row_l2, out);
+  k_output<D, S><<<std::max(blocks, 1), 256, 0, s>>>((const S*)T, dinv, st, row0, N, dc, row_l2, out);
   return after_launch("k_output");
 }
 
@@ -1679,7 +1681,7 @@ struct Ops {
   igp_status (*layer)(const LayerArgs&, cudaStream_t);
   int (*tma_grid)(int32_t);
   igp_status (*layer_tma)(const LayerArgs&, cudaStream_t);
-  igp_status (*output)(const void*, const float*, const float*, int32_t, int, int, float*, cudaStream_t);
+  igp_status (*output)(const void*, const float*, const float*, int32_t, int32_t, int, int, float*, cudaStream_t);
   igp_status (*prescale)(const void*, const float*, int32_t, int32_t, int32_t, void*, cudaStream_t);
 };
 
@@ -1944,7 +1946,7 @@ igp_status run_ffp(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t seed
   }
   {
     PhaseTimer pt(prof, IGP_PHASE_OUTPUT, s);
-    IGP_TRY(ops.output(cur, g->dinv, st_prev, N, dc, o.out_row_l2, out_dev, s));
+    IGP_TRY(ops.output(cur, g->dinv, st_prev, o.out_row_begin, N, dc, o.out_row_l2, out_dev, s));
   }
   // the device error word of this call, read by igp_graph_sync / host-output calls
   IGP_TRY_CUDA(cudaMemcpyAsync(g->err_host, err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -2231,6 +2233,10 @@ extern "C" igp_status igp_embed_noalloc(const int32_t* row_ptr, const int32_t* c
     set_error("igp_embed_noalloc: opts->profile and opts->chunk_cols are not supported here (leave them 0)");
     return IGP_E_INVAL;
   }
+  if (o.out_row_begin < 0 || o.out_row_begin > N) {
+    set_error("igp_embed_noalloc: opts->out_row_begin=%d outside [0, N=%d]", o.out_row_begin, N);
+    return IGP_E_INVAL;
+  }
   Ops ops;
   if (!get_ops(d, o.storage, &ops)) {
     set_error("igp_embed_noalloc: d=%d unsupported (8, 16, 32, 64, 128)", d);
@@ -2311,5 +2317,5 @@ extern "C" igp_status igp_embed_noalloc(const int32_t* row_ptr, const int32_t* c
     cur = dst;
     st_prev = st;
   }
-  return ops.output(cur, dinv, st_prev, N, d, o.out_row_l2, out, s);
+  return ops.output(cur, dinv, st_prev, o.out_row_begin, N, d, o.out_row_l2, out, s);
 }

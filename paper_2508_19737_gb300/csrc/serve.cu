@@ -174,7 +174,7 @@ void settle(igp_server* sv, Req* q) {
 // outside what batches support.
 bool batchable(const igp_request& r) {
   return r.opts.chunk_cols == 0 && (r.opts.gather == IGP_GATHER_AUTO || r.opts.gather == IGP_GATHER_LSU) &&
-         r.opts.reserved_test == 0;
+         r.opts.reserved_test == 0 && r.opts.out_row_begin == 0;
 }
 bool same_ffp(const igp_request& a, const igp_request& b) {
   return a.tau == b.tau && a.L == b.L && a.d == b.d && a.opts.alpha == b.opts.alpha &&
