@@ -65,3 +65,17 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", text, flags=re.M), f
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library every call raises: there is no CPU or PyTorch fallback."""
+    import numpy as np
+    from paper_2508_19737_gb300 import api
+    monkeypatch.setattr(api, "LIB_PATH", str(tmp_path / "libigp.so"))
+    monkeypatch.setattr(api, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        api.lib()
+    with pytest.raises(RuntimeError, match="missing"):
+        api.graph_build(np.zeros(1, np.int32), np.zeros(1, np.int32), 2)
+    with pytest.raises(RuntimeError, match="missing"):
+        api.embed_opts()
