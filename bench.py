@@ -2,7 +2,7 @@
 
 A step is one pass of the whole hot path over one synthetic graph: CSR
 construction from the device-resident edge list, Eq. 1 degree factors, the
-Theta draw, L Eq. 4 layers and the sigmoid output (Alg. 1, lines 1-6). The
+Theta draw, L Eq. 4 layers and the sigmoid output (Alg. 1 up to its clustering step). The
 metric is edge*dim*layer/s = nnz * d * L per step / step time, nnz counting
 the directed CSR entries (twice the undirected edges).
 
@@ -17,6 +17,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -92,21 +93,28 @@ def layer_bytes(N, nnz, d, sb):
     return 4 * nnz + 4 * (N + 1) + 4 * N + 2 * N * d * sb
 
 
+def code_hash(text):
+    """sha256 prefix of C/CUDA source with its comments and blank space removed: edits of comments
+    alone keep the hash, any change to the code changes it."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    text = "\n".join(" ".join(line.split()) for line in text.splitlines() if line.strip())
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
+
+
 def kernel_source_hash():
-    h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2508_19737_gb300", "csrc", "ffp.cu"), "rb") as f:
-        h.update(f.read())
-    return h.hexdigest()[:16]
+    with open(os.path.join(ROOT, "paper_2508_19737_gb300", "csrc", "ffp.cu")) as f:
+        return code_hash(f.read())
 
 
 def recorded_traffic(workload, storage):
     """Per-launch DRAM bytes of k_layer from the committed ncu summary, if it was taken
-    on the current kernel source; else None."""
+    on the current kernel code (comments aside); else None."""
     try:
         with open(PROFILE_SUMMARY) as f:
             j = json.load(f)
         e = j["entries"][f"{workload}/{storage}"]
-        if e.get("ffp_cu_sha256_16") != kernel_source_hash():
+        if e.get("ffp_cu_code_sha256_16") != kernel_source_hash():
             return None
         return float(e["dram_bytes_per_launch"])
     except Exception:

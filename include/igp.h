@@ -4,10 +4,10 @@
  * Partitioning via Spectral Graph Neural Networks with Negative Corrections",
  * arXiv 2508.19737.
  *
- * What the library computes (Alg. 1, lines 1-6):
+ * What the library computes (Alg. 1 up to its clustering step):
  *   A       symmetric binary adjacency of an undirected simple graph (Sec. II)
  *   D_tau   Eq. 1 for tau < 0: deg_i - min(|tau|, deg_i - eps); deg_i + tau otherwise (Sec. I)
- *   Z^(0)   Theta ~ N(0, 1/d), drawn from a seed on the device (Alg. 1, line 2)
+ *   Z^(0)   Theta ~ N(0, 1/d), drawn from a seed on the device (the random input of Alg. 1)
  *   Z^(l)   ZNorm(tanh(theta Z^(l-1) + alpha D_tau^{-1/2} A D_tau^{-1/2} Z^(l-1))), l = 1..L
  *           (Eq. 2-4; the paper's low-pass filter is (alpha, theta) = (1, 0.1))
  *   out     sigmoid(Z^(L)) (Eq. 4), optionally divided by its row L2 norm
@@ -64,7 +64,7 @@ typedef int32_t igp_status;
 
 /* Phases timed by an igp_profile (device time between CUDA events). */
 #define IGP_PHASE_DINV   0  /* Eq. 1 degree factors (fp64 on the device) */
-#define IGP_PHASE_THETA  1  /* Theta generation (Alg. 1, line 2) */
+#define IGP_PHASE_THETA  1  /* Theta generation (the random input of Alg. 1) */
 #define IGP_PHASE_LAYER  2  /* one Eq. 4 layer: gather-SpMM + tanh + column statistics */
 #define IGP_PHASE_OUTPUT 3  /* sigmoid(ZNorm(T^(L))) */
 #define IGP_PHASE_BUILD  4  /* whole CSR construction from an edge list */
@@ -94,7 +94,7 @@ typedef struct igp_embed_opts {
   int32_t out_row_begin;/* first output row, 0 (default) .. N: the call writes rows out_row_begin .. N-1
                            of Z~ (out row 0 = graph row out_row_begin), so `out` holds (N - out_row_begin)
                            x d values. After igp_graph_append grew the graph from N_old nodes, N_old
-                           extracts the new nodes' rows (Alg. 2 l.8). The FFP and its statistics still
+                           extracts the new nodes' rows (as each step of Alg. 2 does). The FFP and its statistics still
                            run over all N rows. With N (no rows) `out` may be NULL and the call is
                            stream-ordered as for a device output. igp_batch_embed takes only 0. */
   const void* x_in;    /* NULL: Theta from `seed`. Else a DEVICE pointer to N x d row-major values in
@@ -133,7 +133,7 @@ igp_status igp_graph_build_profiled(const int32_t* src, const int32_t* dst, int6
                                     void* stream, igp_profile* profile, igp_graph** out);
 
 /*
- * Streaming update (Alg. 2, lines 1-2): merge an increment of undirected edges into the graph's
+ * Streaming update (the merge of each step of Alg. 2): merge an increment of undirected edges into the graph's
  * device-resident CSR, growing it to N_new >= N nodes (new nodes start without edges). The result
  * is the CSR igp_graph_build would give for all edges so far and N_new (sorted, deduplicated,
  * no self-loops). Cached per-graph state (degree factors, processing order) is refreshed on the
@@ -163,7 +163,7 @@ igp_status igp_graph_sync(igp_graph* g);
 void igp_graph_free(igp_graph* g);
 
 /*
- * Theta of Alg. 1, line 2, exactly as igp_embed draws it, as fp32 [N][d] (host or device):
+ * Theta of Alg. 1 (its random input), exactly as igp_embed draws it, as fp32 [N][d] (host or device):
  * Philox4x64-10 (Salmon et al., SC 2011) on counter (i, c/8, 0, 0) with key (seed, 0); its four
  * 64-bit words are split into eight 32-bit halves w_k (low half first); u_k = ((w_k >> 8) + 1) 2^-24;
  * Box-Muller on (u_{2p}, u_{2p+1}) in fp32 gives columns 8(c/8) + 0..7; times x_scale
@@ -172,7 +172,7 @@ void igp_graph_free(igp_graph* g);
 igp_status igp_generate_x(uint64_t seed, int32_t N, int32_t d, double x_scale, float* out, void* stream);
 
 /*
- * One FFP (Alg. 1, lines 1-6) on graph g:
+ * One FFP (Alg. 1 up to its clustering step) on graph g:
  *   tau  : degree correction (Eq. 1 for tau < 0), any finite value
  *   L    : number of layers, 0 <= L <= 10000 (L = 0 gives sigmoid(Theta))
  *   d    : embedding width, one of 8, 16, 32, 64, 128
@@ -205,7 +205,7 @@ igp_status igp_batch_info(const igp_batch* b, int32_t* G, int32_t* N_total, int6
                           int32_t* row_offsets);
 
 /*
- * One FFP per graph of the batch (Alg. 1, lines 1-6), all graphs in the same launches:
+ * One FFP per graph of the batch (Alg. 1 up to its clustering step), all graphs in the same launches:
  *   seeds : host array of G Theta seeds (graph g's rows draw Theta with seeds[g] and local row ids)
  *   out   : N_total x d fp32 (host or device); graph g's rows at row_offsets[g] ..
  *   opts  : as igp_embed, except x_in, chunk_cols and TMA gathers (not supported here)

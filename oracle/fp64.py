@@ -146,7 +146,7 @@ def round_bf16(x):
 
 
 # ----------------------------------------------------------------------------
-# Alg. 1, lines 1-6
+# Alg. 1 up to its clustering step
 # ----------------------------------------------------------------------------
 def ffp(row_ptr, col, X, tau, L, alpha=1.0, theta=0.1, eps=1e-3, ddof=1,
         out_row_l2=False, storage="f64", return_layers=False):
@@ -164,7 +164,7 @@ def ffp(row_ptr, col, X, tau, L, alpha=1.0, theta=0.1, eps=1e-3, ddof=1,
     X = np.asarray(X, dtype=np.float64)
     if X.shape[0] != N:
         raise ValueError("X must have N rows")
-    # line 1: D_tau via Eq. 1, and the normalised adjacency of Eq. 3
+    # degree correction: D_tau via Eq. 1, and the normalised adjacency of Eq. 3
     dinv = inv_sqrt_degrees(degree_correction(degrees(row_ptr), tau, eps))
     Ahat = normalized_adjacency(row_ptr, col, dinv)
     if storage == "bf16":
@@ -172,10 +172,10 @@ def ffp(row_ptr, col, X, tau, L, alpha=1.0, theta=0.1, eps=1e-3, ddof=1,
         store = lambda a: round_bf16(sc * a) / sc  # noqa: E731
     else:
         store = lambda a: a  # noqa: E731
-    # lines 2-3: Z^(0) = Theta
+    # random input: Z^(0) = Theta
     Z = store(X)
     layers = []
-    # lines 4-5: L layers of Eq. 4
+    # L layers of Eq. 4
     for _ in range(L):
         T = np.tanh(conv(Ahat, Z, alpha, theta))
         _, mu, s = znorm(T, ddof)
@@ -185,7 +185,7 @@ def ffp(row_ptr, col, X, tau, L, alpha=1.0, theta=0.1, eps=1e-3, ddof=1,
         Z[:, nz] = (Ts[:, nz] - mu[nz]) / s[nz]
         if return_layers:
             layers.append((T, mu, s))
-    # line 6: output
+    # output: sigmoid of the last ZNorm
     out = sigmoid(Z)
     if out_row_l2:
         out = out / np.linalg.norm(out, axis=1, keepdims=True)
@@ -201,10 +201,10 @@ def ffp_from_edges(src, dst, N, X, tau, L, **kw):
 
 
 # ----------------------------------------------------------------------------
-# Alg. 2, lines 1-7 (streaming): the cumulative graph after each increment
+# Alg. 2 (streaming): the cumulative graph after each increment
 # ----------------------------------------------------------------------------
 def stream_snapshots(increments):
-    """Cumulative topology of Alg. 2, line 1.
+    """Cumulative topology of Alg. 2 (each step adds its increment to the graph so far).
 
     increments: list of (src, dst, N_t) with N_t the node count after step t.
     Yields (row_ptr, col, N_t) of the merged graph after each step.

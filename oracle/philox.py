@@ -1,10 +1,10 @@
-"""Random input Theta ~ N(0, 1/d) of Alg. 1 (line 2) and Eq. 4's Z^(0), from a seed.
+"""Random input Theta ~ N(0, 1/d) of Alg. 1 and Eq. 4's Z^(0), from a seed.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring): the product library has
 its own, separately written generator and never imports this module.
 
 The paper only says that Z^(0) = Theta is Gaussian noise with variance 1/d
-(Sec. III-A, Eq. 4; Alg. 1, line 2). To make that noise reproducible on both
+(Sec. III-A, Eq. 4; the random input of Alg. 1). To make that noise reproducible on both
 sides, row i / column c of Theta is a fixed function of (seed, i, c):
 
 * Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
@@ -22,8 +22,8 @@ sides, row i / column c of Theta is a fixed function of (seed, i, c):
   variance 1/d) unless another scale is asked for.
 
 Rows depend only on (seed, i), so the rows of old nodes do not change when a
-streaming graph grows (Alg. 2, line 3 still draws a fresh N(0, 1/d) matrix for a
-fresh seed).
+streaming graph grows (each step of Alg. 2 still draws a fresh N(0, 1/d) matrix
+for a fresh seed).
 """
 import numpy as np
 

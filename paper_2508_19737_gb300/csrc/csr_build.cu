@@ -1145,7 +1145,7 @@ igp_status build_csr(const int32_t* src, const int32_t* dst, int64_t M, int32_t 
   return build_csr_atomic(src, dst, M, N, s, g);
 }
 
-// Alg. 2, lines 1-2: merge an increment of edges (and new nodes up to N_new) into g.
+// Alg. 2, the merge of each step: merge an increment of edges (and new nodes up to N_new) into g.
 igp_status append_csr(igp_graph* g, const int32_t* src, const int32_t* dst, int64_t M, int32_t N_new, cudaStream_t s) {
   igp_graph inc;
   IGP_TRY(build_csr(src, dst, M, N_new, s, &inc));  // validates ids, sorts and dedups the increment

@@ -1,8 +1,8 @@
-// The feed-forward propagation (FFP) of InfraredGP, Alg. 1 lines 1-6:
+// The feed-forward propagation (FFP) of InfraredGP, Alg. 1 up to its clustering step:
 //   k_dinv        Eq. 1 degree correction D_tau and D_tau^{-1/2} (fp64, rounded to fp32)
 //   k_wsum        w_i = sum_{j in N(i)} dinv_j (fp32), once per graph and tau
 //   k_deg_*       rows in order of decreasing degree, once per graph
-//   k_theta       Z^(0) = Theta ~ N(0, 1/d): Philox4x64-10 + Box-Muller (Alg. 1, line 2)
+//   k_theta       Z^(0) = Theta ~ N(0, 1/d): Philox4x64-10 + Box-Muller (the random input of Alg. 1)
 //   k_layer       one Eq. 4 layer: T^(l) = tanh(theta Z + alpha Ahat Z), Z = ZNorm(T^(l-1)),
 //                 fused with the column statistics of T^(l) that the next ZNorm needs
 //   k_layer_tma   the same layer with the neighbour rows brought in by the TMA engine
@@ -129,7 +129,7 @@ __global__ void k_dinv(const int32_t* __restrict__ row_ptr, int32_t N, double ta
   }
 }
 
-// ------------------------------------------------------------------ Theta (Alg. 1, line 2)
+// ------------------------------------------------------------------ Theta (random input of Alg. 1)
 // Philox4x64-10 (Salmon et al., SC 2011): round multipliers and Weyl key increments.
 constexpr uint64_t kPhiloxM0 = 0xD2E7470EE14C6C93ull;
 constexpr uint64_t kPhiloxM1 = 0xCA5A826395121157ull;
@@ -1097,7 +1097,7 @@ __global__ void k_output(const S* __restrict__ T, const float* __restrict__ dinv
   const int chunk = lane % G, sub = lane / G;
   const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  // rows row0 .. N-1 (Alg. 2 l.8 extracts the newest nodes' rows); out row 0 is row row0
+  // rows row0 .. N-1 (Alg. 2 extracts the newest nodes' rows); out row 0 is row row0
   for (int64_t base = row0 + warp_id * RPW; base < N; base += nw * RPW) {  // warp-uniform loop
     const int64_t i = base + sub;
     const bool ok = i < N;

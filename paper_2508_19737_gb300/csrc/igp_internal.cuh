@@ -166,7 +166,7 @@ struct LayerArgs {
 igp_status ensure_perm(igp_graph* g, cudaStream_t s);
 // dinv and w for (tau, eps), cached on the graph.
 igp_status compute_dinv(igp_graph* g, double tau, double eps, cudaStream_t s, Profile* prof);
-// Theta (Alg. 1, line 2) into `out` in the storage type, in column blocks of dc columns
+// Theta (the random input of Alg. 1) into `out` in the storage type, in column blocks of dc columns
 // (dc = d: row-major), multiplied row-wise by dinv if non-NULL.
 igp_status launch_theta(uint64_t seed, int32_t N, int32_t d, int32_t dc, float x_scale, int storage,
                         const float* dinv, void* out, cudaStream_t s);

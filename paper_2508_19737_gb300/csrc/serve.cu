@@ -1,5 +1,5 @@
 // Serving loop (igp_server_*): requests to embed graphs, or to grow a resident graph by an
-// edge increment and re-embed it (Alg. 2, lines 1-7), are queued, admitted into a fixed
+// edge increment and re-embed it (the merge and FFP of a step of Alg. 2), are queued, admitted into a fixed
 // number of slots as device memory and slots free up, and run concurrently: every slot
 // is a host worker thread with its own CUDA stream that builds or grows the request's
 // CSR and embeds the graph, so the GPU work of admitted requests overlaps. Optionally

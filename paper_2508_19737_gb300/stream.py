@@ -4,18 +4,18 @@ overlapped with the next step's FFP.
 Step t, for an increment (V_t, E_t) whose new nodes carry the ids N_(t-1) .. N_t - 1 (the snowball
 model of Sec. II numbers nodes in arrival order):
 
-* l.1-2: the increment is merged into the device-resident cumulative CSR (igp_graph_append; the
+* merge: the increment is merged into the device-resident cumulative CSR (igp_graph_append; the
   first step builds it, which is Alg. 1 on (V_1, E_1));
-* l.3-7: one FFP over all N_t nodes with a fresh Theta (seed + t);
-* l.8: only the new nodes' rows leave the device (igp_embed with out_row_begin = N_(t-1));
-* l.9: the clusterer is partially fitted on those rows;
-* l.10: they are appended to the rows kept from earlier steps (old nodes keep the rows of the step
+* embed: one FFP over all N_t nodes with a fresh Theta (seed + t);
+* extract: only the new nodes' rows leave the device (igp_embed with out_row_begin = N_(t-1));
+* fit: the clusterer is partially fitted on those rows;
+* keep: they are appended to the rows kept from earlier steps (old nodes keep the rows of the step
   that added them);
-* l.11: the clusterer assigns a block to every node so far.
+* assign: the clusterer assigns a block to every node so far.
 
-Lines 1-8 run on the calling thread (the library call releases the interpreter lock while the GPU
-works); lines 9-11 run in step order on one host thread, so step t's clustering overlaps step t+1's
-FFP. Any object with `partial_fit(X)` and `predict(X)` is a clusterer; `birch()` makes the
+Merge, embed and extract run on the calling thread (the library call releases the interpreter lock
+while the GPU works); fit, keep and assign run in step order on one host thread, so step t's
+clustering overlaps step t+1's FFP. Any object with `partial_fit(X)` and `predict(X)` is a clusterer; `birch()` makes the
 scikit-learn BIRCH the paper uses (Sec. IV-A) when that package is installed.
 """
 import queue
@@ -41,10 +41,12 @@ def birch(threshold=0.5, branching_factor=50):
 class StreamingPartitioner:
     """Alg. 2 over a stream of edge increments; see the module docstring.
 
-    step(src, dst, N_t) runs lines 1-8 and queues lines 9-11, returning the step index t;
+    step(src, dst, N_t) runs merge, embed and extract and queues fit, keep and assign, returning
+    the step index t;
     labels(t) waits for step t's partition C^(t) (one block id per node 0 .. N_t - 1).
-    timings[t] holds the seconds of the GPU part ("ffp_s", lines 1-8 including the copy of the new
-    rows) and of the host part ("cluster_s", lines 9-11) of each finished step.
+    timings[t] holds the seconds of the GPU part ("ffp_s": merge, embed and extract, including the
+    copy of the new rows) and of the host part ("cluster_s": fit, keep and assign) of each finished
+    step.
     """
 
     def __init__(self, clusterer, tau=-0.5, L=10, d=64, seed=0, storage="bf16", stream=None, **opts):
@@ -62,7 +64,7 @@ class StreamingPartitioner:
         self._worker = threading.Thread(target=self._cluster_loop, name="igp-stream-cluster", daemon=True)
         self._worker.start()
 
-    # lines 1-8 ------------------------------------------------------------------------------
+    # merge, embed, extract -----------------------------------------------------------------
     def step(self, src, dst, N_t):
         self._raise_pending()
         t = self._t
@@ -80,7 +82,7 @@ class StreamingPartitioner:
         self._q.put((t, rows))
         return t
 
-    # lines 9-11 -----------------------------------------------------------------------------
+    # fit, keep, assign ---------------------------------------------------------------------
     def _cluster_loop(self):
         while True:
             item = self._q.get()
@@ -90,12 +92,12 @@ class StreamingPartitioner:
             try:
                 t0 = time.perf_counter()
                 if rows.shape[0]:
-                    self.clusterer.partial_fit(rows)  # l.9
-                self._rows.append(rows)  # l.10
+                    self.clusterer.partial_fit(rows)  # fit
+                self._rows.append(rows)  # keep
                 kept = np.concatenate(self._rows) if len(self._rows) > 1 else self._rows[0]
                 if len(self._rows) > 1:
                     self._rows = [kept]
-                lab = np.asarray(self.clusterer.predict(kept))  # l.11
+                lab = np.asarray(self.clusterer.predict(kept))  # assign
                 dt = time.perf_counter() - t0
                 with self._done:
                     self.timings[t]["cluster_s"] = dt

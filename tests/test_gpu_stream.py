@@ -1,4 +1,4 @@
-"""Streaming (Alg. 2, lines 1-7): a device-resident graph grown by edge increments equals, after
+"""Streaming (the merge and FFP of each step of Alg. 2): a device-resident graph grown by edge increments equals, after
 every step, the graph built from scratch from all edges so far (CSR bit-exact against the FP64
 oracle's cumulative snapshot), and its embedding equals the fresh build's bit for bit."""
 import numpy as np
@@ -73,7 +73,7 @@ def test_append_rejects_bad_input_and_keeps_graph(api):
 
 
 def test_new_node_rows_extracted_on_the_device(api):
-    """Alg. 2 l.8: with out_row_begin = N_(t-1) igp_embed writes only the new nodes' rows, bit for bit
+    """Alg. 2 extracts the new nodes' rows: with out_row_begin = N_(t-1) igp_embed writes only the new nodes' rows, bit for bit
     the rows N_(t-1).. of the whole embedding, into device, page-locked and pageable outputs."""
     import torch
     g = synth.dcsbm(9000, 10, 18, 2.5, 5, seed=51)

@@ -31,7 +31,7 @@ def _golden(name):
 
 
 # ---------------------------------------------------------------------------
-# Philox4x64-10 and the Gaussian input (Alg. 1 line 2)
+# Philox4x64-10 and the Gaussian input (the random input of Alg. 1)
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("ctr,key", [
     ([0, 0, 0, 0], [0, 0]),

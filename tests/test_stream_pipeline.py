@@ -1,4 +1,4 @@
-"""Host logic of the streaming partitioner (Alg. 2 l.8-11), with the library calls replaced by the
+"""Host logic of the streaming partitioner (the extraction of new rows and the clustering steps of Alg. 2), with the library calls replaced by the
 FP64 oracle: each step hands exactly the new nodes' rows of that step's FFP to partial_fit, keeps
 the old rows, predicts every node, runs the clustering of step t while step t+1's FFP is under way,
 and reports clustering failures on the caller's thread. (The CUDA path itself is covered by the
@@ -93,12 +93,12 @@ def test_each_step_fits_the_new_rows_and_predicts_every_node(monkeypatch):
         acc_d.append(d)
         Z = oracle.ffp_from_edges(np.concatenate(acc_s), np.concatenate(acc_d), n, oracle.theta_input(40 + t, n, 8),
                                   -0.5, 3).astype(np.float32)
-        assert fake.embedded[t] == (40 + t, n_prev)  # fresh Theta per step (l.3), new rows only (l.8)
-        assert np.array_equal(cl.fits[t], Z[n_prev:])  # l.9
+        assert fake.embedded[t] == (40 + t, n_prev)  # fresh Theta per step, new rows only
+        assert np.array_equal(cl.fits[t], Z[n_prev:])  # partial fit on the new rows
         assert labs[t].shape == (n,)
         n_prev = n
-    kept = np.concatenate(cl.fits)  # l.10: old nodes keep the rows of the step that added them
-    assert np.array_equal(labs[-1], cl.predict(kept))  # l.11
+    kept = np.concatenate(cl.fits)  # old nodes keep the rows of the step that added them
+    assert np.array_equal(labs[-1], cl.predict(kept))  # every node assigned
     assert set(cl.threads) == {"igp-stream-cluster"}
     assert all(sp.timings[t]["ffp_s"] >= 0 and sp.timings[t]["cluster_s"] >= 0 for t in steps)
 
