@@ -20,6 +20,9 @@ What is computed (Qin, Li, Cui, Pei, "InfraredGP", arXiv 2508.19737):
 
 Readings where the paper is silent (each is an option here and on the GPU):
   * ZNorm's standard deviation uses ddof=1 by default (ddof=0 on request).
+    Parity unpinned as to which divisor the authors used: the paper does not
+    say, and no printed value decides it (both are pinned against the closed
+    forms of their own divisor).
   * A column with zero standard deviation normalises to 0.
   * A node with D_tau == 0 (tau = 0, isolated) gets D_tau^{-1/2} = 0; its row
     of A is empty, so nothing else depends on it.
