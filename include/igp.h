@@ -299,6 +299,12 @@ igp_status igp_poll(igp_server* sv, uint64_t ticket, int32_t* state, double* lat
 igp_status igp_wait(igp_server* sv, uint64_t ticket, double timeout_s, int32_t* state, double* latency_s);
 /* Cancel a queued request (IGP_E_BUSY once it runs). */
 igp_status igp_cancel(igp_server* sv, uint64_t ticket);
+/* Drop the server's record of a finished (done, failed or cancelled) request, so that a long-running
+ * server does not keep one record per request it ever served. Afterwards the ticket is unknown
+ * (IGP_E_INVAL from igp_poll / igp_wait / igp_cancel); the request's output is untouched. Errors:
+ * IGP_E_INVAL (unknown ticket), IGP_E_BUSY (the request is queued or running, or another thread is
+ * inside igp_wait on it). */
+igp_status igp_server_forget(igp_server* sv, uint64_t ticket);
 /* Free a resident graph (waits for a request running on it). */
 igp_status igp_server_release(igp_server* sv, int64_t graph_id);
 igp_status igp_server_get_stats(igp_server* sv, igp_server_stats* stats);

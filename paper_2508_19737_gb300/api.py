@@ -137,6 +137,7 @@ _SIGS = {
     "igp_wait": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
                                   ctypes.POINTER(ctypes.c_double)]),
     "igp_cancel": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64]),
+    "igp_server_forget": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint64]),
     "igp_server_release": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int64]),
     "igp_server_get_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
     "igp_profile_create": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_void_p)]),
@@ -457,6 +458,14 @@ class Server:
 
     def result(self, ticket):
         return self._outs[ticket]
+
+    def forget(self, ticket):
+        """igp_server_forget: drop a finished request's record in the server and this wrapper's
+        reference to its output, which is returned. Call it once a result has been read, so that
+        a long-running server keeps nothing per past request. Raises IgpError (IGP_E_BUSY) while
+        the request is queued or running."""
+        _check(lib().igp_server_forget(self.handle, ticket))
+        return self._outs.pop(ticket, None)
 
     def cancel(self, ticket):
         _check(lib().igp_cancel(self.handle, ticket))

@@ -40,6 +40,7 @@ struct Req {
   size_t est = 0;
   igp_graph* g = nullptr;  // the request's graph once its CSR is built or grown
   bool embedded = false;   // set by the batcher once the result is in r.out (or failed)
+  int waiters = 0;         // callers inside igp_wait on this request (igp_server_forget refuses then)
   Clock::time_point t_submit, t_start, t_done;
 };
 
@@ -490,11 +491,34 @@ igp_status igp_wait(igp_server* sv, uint64_t ticket, double timeout_s, int32_t* 
   }
   Req* q = it->second;
   auto finished = [&] { return q->state >= IGP_REQ_DONE; };
+  q->waiters += 1;  // keeps the record alive while this thread sleeps without the lock
   if (timeout_s < 0)
     sv->cv.wait(lk, finished);
   else
     sv->cv.wait_for(lk, std::chrono::duration<double>(timeout_s), finished);
+  q->waiters -= 1;
   return report(q, state, latency_s);
+}
+
+igp_status igp_server_forget(igp_server* sv, uint64_t ticket) {
+  clear_error();
+  if (!sv) return IGP_E_INVAL;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) {
+    set_error("igp_server_forget: unknown ticket %llu", (unsigned long long)ticket);
+    return IGP_E_INVAL;
+  }
+  Req* q = it->second;
+  // a finished record is no longer referenced by the queue, the batcher or a worker; only
+  // callers of igp_wait may still hold it
+  if (q->state < IGP_REQ_DONE || q->waiters > 0) {
+    set_error("igp_server_forget: request %llu is queued, running or being waited on", (unsigned long long)ticket);
+    return IGP_E_BUSY;
+  }
+  sv->reqs.erase(it);
+  delete q;
+  return IGP_OK;
 }
 
 igp_status igp_cancel(igp_server* sv, uint64_t ticket) {

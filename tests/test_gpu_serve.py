@@ -114,6 +114,34 @@ def test_cancel_and_failures(api):
     sv.close()
 
 
+
+def test_forget_finished_requests(api):
+    """A long-running server drops the records of requests whose results were read: a finished
+    request can be forgotten (its output stays as it was), a queued one cannot, and a forgotten
+    ticket is unknown afterwards."""
+    g = synth.dcsbm(20000, 8, 20, 2.5, 5, seed=44)
+    sv = api.Server(slots=1)
+    ts = [sv.submit(g.src, g.dst, g.N, -0.5, 10, 64, k) for k in range(16)]
+    with pytest.raises(api.IgpError) as e:  # still queued behind fifteen others on one slot
+        sv.forget(ts[-1])
+    assert e.value.status == api.IGP_E_BUSY
+    for t in ts:
+        assert sv.wait(t)[0] == "done"
+    first = sv.result(ts[0]).copy()
+    out = sv.forget(ts[0])
+    assert np.array_equal(out, first)
+    assert sv.poll(ts[0])[2] == api.IGP_E_INVAL
+    with pytest.raises(api.IgpError) as e:
+        sv.forget(ts[0])
+    assert e.value.status == api.IGP_E_INVAL
+    for t in ts[1:]:
+        sv.forget(t)
+    t = sv.submit(g.src, g.dst, g.N, -0.5, 10, 64, 0)  # the same request as the first, served again
+    assert sv.wait(t)[0] == "done"
+    assert np.array_equal(sv.forget(t), first)
+    assert sv.stats()["completed"] == 17
+    sv.close()
+
 def test_continuous_batches_equal_each_request_alone(api):
     """Many compatible small requests in flight at once are embedded in shared batches; each
     result equals igp_embed of that graph alone (to fp32 rounding)."""
