@@ -45,7 +45,33 @@ def _mut_dinv_same_side(row_ptr, col, dinv):
     return (sp.diags(np.asarray(dinv) ** 2) @ A).tocsr()
 
 
+def _mut_global_znorm(T, ddof=1):
+    # "standard deviation of entries" misread as one mean and std over the whole matrix
+    T = np.asarray(T, dtype=np.float64)
+    mu, sd = T.mean(), T.std(ddof=ddof)
+    d = T.shape[1]
+    return (T - mu) / sd, np.full(d, mu), np.full(d, sd)
+
+
+def _mut_clamp_to_zero(deg, tau, eps=1e-3):
+    # Eq. 1 without its eps: nodes with deg <= |tau| get D_tau = 0
+    deg = np.asarray(deg, dtype=np.float64)
+    return deg - np.minimum(abs(tau), deg) if tau < 0 else deg + tau
+
+
+def _mut_inverse_not_sqrt(Dtau):
+    # D_tau^{-1} where D_tau^{-1/2} is meant
+    Dtau = np.asarray(Dtau, dtype=np.float64)
+    out = np.zeros_like(Dtau)
+    out[Dtau > 0] = 1.0 / Dtau[Dtau > 0]
+    return out
+
+
 MUTATIONS = {
+    "ZNorm over all entries": ("znorm", _mut_global_znorm),
+    "Eq. 1 clamped to 0": ("degree_correction", _mut_clamp_to_zero),
+    "D^-1 instead of D^-1/2": ("inv_sqrt_degrees", _mut_inverse_not_sqrt),
+    "alpha and theta swapped": ("conv", lambda Ahat, Z, alpha=1.0, theta=0.1: alpha * Z + theta * (Ahat @ Z)),
     "self term dropped": ("conv", lambda Ahat, Z, alpha=1.0, theta=0.1: alpha * (Ahat @ Z)),
     "alpha sign flipped": ("conv", lambda Ahat, Z, alpha=1.0, theta=0.1: theta * Z - alpha * (Ahat @ Z)),
     "tau ignored": ("degree_correction", lambda deg, tau, eps=1e-3: np.asarray(deg, dtype=float)),
