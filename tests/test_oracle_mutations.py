@@ -46,7 +46,7 @@ def _mut_dinv_same_side(row_ptr, col, dinv):
 
 
 def _mut_global_znorm(T, ddof=1):
-    # "standard deviation of entries" misread as one mean and std over the whole matrix
+    # Eq. 4 read as one mean and one std over the whole matrix rather than per column
     T = np.asarray(T, dtype=np.float64)
     mu, sd = T.mean(), T.std(ddof=ddof)
     d = T.shape[1]
