@@ -44,3 +44,14 @@ def test_max_over_ranks_and_replica_rate_two_gloo_ranks():
 def test_single_rank_is_the_identity():
     assert bench.max_over_ranks(3.5, 1) == 3.5
     assert bench.replica_rate(2.0, 3, 1, 1000.0) == pytest.approx(6.0)
+
+
+def test_kernel_hash_ignores_comments_only():
+    """The recorded ncu traffic stays valid across edits of comments, and no longer applies once
+    the code changes."""
+    src = "// header\n__global__ void k(int* p) {  /* body */\n  p[0] = 1;  // store\n}\n"
+    same = "// other words\n__global__ void k(int* p) {\n  /* a\n  longer note */ p[0] = 1;\n}\n"
+    changed = "// header\n__global__ void k(int* p) {\n  p[0] = 2;\n}\n"
+    assert bench.code_hash(src) == bench.code_hash(same)
+    assert bench.code_hash(src) != bench.code_hash(changed)
+    assert len(bench.kernel_source_hash()) == 16
