@@ -33,7 +33,7 @@ import scipy.sparse as sp
 
 __all__ = [
     "build_csr", "degrees", "degree_correction", "inv_sqrt_degrees",
-    "normalized_adjacency", "conv", "conv_rows", "znorm", "sigmoid", "round_bf16",
+    "normalized_adjacency", "conv", "conv_rows", "znorm", "sigmoid", "round_bf16", "bf16_store",
     "ffp", "ffp_from_edges", "stream_snapshots", "dense_adjacency",
     "corrected_laplacian",
 ]
@@ -151,15 +151,29 @@ def round_bf16(x):
 # ----------------------------------------------------------------------------
 # Alg. 1 up to its clustering step
 # ----------------------------------------------------------------------------
+def bf16_store(a, dinv, layout="row_scaled"):
+    """The values read back after rows of `a` (N x d) were stored in BF16.
+
+    layout="row_scaled": row i is held as dinv_i * a_i (a_i where dinv_i = 0),
+    so the rounding acts on that product and is undone by the division.
+    layout="plain": each value a_ij is rounded on its own.
+    """
+    if layout == "plain":
+        return round_bf16(a)
+    sc = np.where(np.asarray(dinv) > 0, dinv, 1.0)[:, None]
+    return round_bf16(sc * a) / sc
+
+
 def ffp(row_ptr, col, X, tau, L, alpha=1.0, theta=0.1, eps=1e-3, ddof=1,
         out_row_l2=False, storage="f64", return_layers=False):
     """One FFP over the graph given in CSR form, on the input X = Theta.
 
     storage="bf16" rounds to BF16 where the GPU stores in BF16: Theta and each
-    layer's tanh output T^(l) are stored row-scaled, as dinv_i * x_i (x_i where
-    dinv_i = 0), so the rounding is applied to that product and undone by the
-    division; the column statistics of a layer are those of its unrounded T^(l).
-    It only separates storage error from bugs; the fp64 result is the contract.
+    layer's tanh output T^(l), in the row-scaled layout of bf16_store; the column
+    statistics of a layer are those of its unrounded T^(l). storage="bf16_plain"
+    rounds the same values one by one instead (bf16_store's plain layout), a
+    second storage of the same precision to compare against. Both only separate
+    storage error from bugs; the fp64 result is the contract.
     Returns Z~ (N x d, fp64), plus per-layer (T, mean, std) if asked.
     """
     row_ptr = np.asarray(row_ptr, dtype=np.int64)
@@ -170,11 +184,13 @@ def ffp(row_ptr, col, X, tau, L, alpha=1.0, theta=0.1, eps=1e-3, ddof=1,
     # degree correction: D_tau via Eq. 1, and the normalised adjacency of Eq. 3
     dinv = inv_sqrt_degrees(degree_correction(degrees(row_ptr), tau, eps))
     Ahat = normalized_adjacency(row_ptr, col, dinv)
-    if storage == "bf16":
-        sc = np.where(dinv > 0, dinv, 1.0)[:, None]
-        store = lambda a: round_bf16(sc * a) / sc  # noqa: E731
-    else:
+    if storage in ("bf16", "bf16_plain"):
+        layout = "row_scaled" if storage == "bf16" else "plain"
+        store = lambda a: bf16_store(a, dinv, layout)  # noqa: E731
+    elif storage == "f64":
         store = lambda a: a  # noqa: E731
+    else:
+        raise ValueError("storage is one of f64, bf16, bf16_plain")
     # random input: Z^(0) = Theta
     Z = store(X)
     layers = []

@@ -147,17 +147,19 @@ def log_uniform_sizes(rng, n, lo, hi):
 def batch_dcsbm(G, n_lo, n_hi, deg_lo, deg_hi, gamma, ratio, seed=0, block_exp=0.4):
     """G independent graphs: N log-uniform on [n_lo, n_hi], blocks = round(N^block_exp),
     mean degree uniform on [deg_lo, deg_hi]; graph g uses SeedSequence(seed).spawn(G)[g]."""
+    return [batch_dcsbm_one(G, n_lo, n_hi, deg_lo, deg_hi, gamma, ratio, g, seed, block_exp) for g in range(G)]
+
+
+def batch_dcsbm_one(G, n_lo, n_hi, deg_lo, deg_hi, gamma, ratio, k, seed=0, block_exp=0.4):
+    """Graph k of batch_dcsbm(G, ...), drawn alone (the same graph)."""
     ss = np.random.SeedSequence(seed)
     rng = np.random.default_rng(ss)
     Ns = log_uniform_sizes(rng, G, n_lo, n_hi)
     degs = rng.uniform(deg_lo, deg_hi, size=G)
-    kids = ss.spawn(G)
-    out = []
-    for g in range(G):
-        N = int(Ns[g])
-        B = max(1, int(round(N ** block_exp)))
-        out.append(dcsbm(N, B, float(degs[g]), gamma, ratio, seed=kids[g]))
-    return out
+    kid = ss.spawn(G)[k]
+    N = int(Ns[k])
+    B = max(1, int(round(N ** block_exp)))
+    return dcsbm(N, B, float(degs[k]), gamma, ratio, seed=kid)
 
 
 def split_increments(graph, T=10, mode="random", seed=0):
@@ -254,6 +256,20 @@ def workload_graph(name):
 def workload_batch(name):
     b = BATCH_WORKLOADS[name]["batch"]
     return batch_dcsbm(b["G"], b["n_lo"], b["n_hi"], b["deg_lo"], b["deg_hi"], b["gamma"], b["ratio"], seed=b["seed"])
+
+
+def workload_batch_graph(name, k):
+    """Graph k of a batch workload, drawn alone."""
+    b = BATCH_WORKLOADS[name]["batch"]
+    return batch_dcsbm_one(b["G"], b["n_lo"], b["n_hi"], b["deg_lo"], b["deg_hi"], b["gamma"], b["ratio"], k,
+                           seed=b["seed"])
+
+
+def workload_batch_sizes(name):
+    """Node counts of every graph of a batch workload (without drawing the graphs)."""
+    b = BATCH_WORKLOADS[name]["batch"]
+    rng = np.random.default_rng(np.random.SeedSequence(b["seed"]))
+    return log_uniform_sizes(rng, b["G"], b["n_lo"], b["n_hi"])
 
 
 # A served stream: G graphs, N log-uniform on [5,000, 1,000,000], blocks round(N^0.4), mean

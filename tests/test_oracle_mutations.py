@@ -117,3 +117,65 @@ def test_planted_generator_mistake_is_caught(monkeypatch, name):
         monkeypatch.setattr(oph, "uniforms_from_words",
                             lambda x: ((np.asarray(x, dtype=np.uint64)[..., [0, 0, 1, 1, 2, 2, 3, 3]] >> np.uint64(40))).astype(float) * 2.0 ** -24)
     assert _some_pin_fails()
+
+
+# ---------------------------------------------------------------------------
+# the BF16-storage variants: their own pins (tests/test_oracle_bf16.py)
+# ---------------------------------------------------------------------------
+from tests import test_oracle_bf16 as bf16_pins  # noqa: E402
+
+BF16_PIN_CALLS = [
+    lambda: bf16_pins.test_bf16_theta_is_rounded_after_row_scaling(),
+    lambda: bf16_pins.test_bf16_layer_statistics_come_from_the_unrounded_layer(),
+    lambda: bf16_pins.test_bf16_equals_per_element_emulation(0, -0.5, 3, "row_scaled"),
+    lambda: bf16_pins.test_bf16_equals_per_element_emulation(3, 2.0, 3, "row_scaled"),
+]
+
+
+def _some_bf16_pin_fails():
+    for call in BF16_PIN_CALLS:
+        try:
+            call()
+        except (AssertionError, ValueError, IndexError):
+            return True
+    return False
+
+
+def _unrounded_first_call(orig):
+    calls = []
+
+    def store(a, dinv, layout="row_scaled"):
+        calls.append(1)
+        return np.asarray(a, dtype=np.float64) if len(calls) == 1 else orig(a, dinv, layout)
+    return store
+
+
+@pytest.mark.parametrize("name", ["rounds the unscaled value", "statistics of the rounded layer",
+                                  "Theta not rounded"])
+def test_planted_bf16_storage_mistake_is_caught(monkeypatch, name):
+    if name == "rounds the unscaled value":
+        monkeypatch.setattr(off, "bf16_store", lambda a, dinv, layout="row_scaled": off.round_bf16(a))
+    elif name == "statistics of the rounded layer":
+        orig = off.znorm
+        monkeypatch.setattr(off, "znorm", lambda T, ddof=1: orig(off.round_bf16(T), ddof))
+    else:
+        # every test call makes a fresh wrapper, so Theta (the first store of an FFP) goes unrounded
+        orig = off.bf16_store
+
+        class _Fresh:
+            def __call__(self, a, dinv, layout="row_scaled"):
+                return self.fn(a, dinv, layout)
+        fresh = _Fresh()
+        real_ffp = off.ffp
+
+        def ffp(*a, **k):
+            fresh.fn = _unrounded_first_call(orig)
+            return real_ffp(*a, **k)
+        monkeypatch.setattr(off, "bf16_store", fresh)
+        monkeypatch.setattr(off, "ffp", ffp)
+        monkeypatch.setattr(oracle, "ffp", ffp)
+    assert _some_bf16_pin_fails(), f"no pin caught: {name}"
+
+
+def test_bf16_pins_pass_unmutated():
+    assert not _some_bf16_pin_fails()
