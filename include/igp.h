@@ -111,6 +111,10 @@ const char* igp_last_error(void);
 /* Number of CUDA kernels this library has launched in this process so far. */
 int64_t igp_launch_count(void);
 
+/* Number of memory allocations (device memory from the library's pool, pinned host words of graph
+ * handles) this library has made in this process so far. */
+int64_t igp_alloc_count(void);
+
 /* Defaults: alpha 1, theta 0.1, eps 1e-3, x_scale 1/sqrt(d), ddof 1, fp32 storage, no row L2. */
 void igp_embed_opts_init(igp_embed_opts* opts);
 
@@ -223,9 +227,11 @@ void igp_batch_free(igp_batch* b);
  * Serving. A server admits requests into `slots` concurrent slots (host worker threads, each with
  * its own CUDA stream, so the GPU work of admitted requests overlaps) as slots and device memory
  * free up: a request starts only if its estimated peak device memory fits the server's budget
- * (free memory at creation minus reserve_bytes) next to the running ones and the resident graphs
- * (a request that finds nothing running starts regardless and fails with IGP_E_NOMEM if the
- * memory is not there). Requests are picked in submission order among those that may start. Resident graphs keep
+ * (free memory at creation minus reserve_bytes) next to the running ones and the resident graphs,
+ * and also fits the device memory free at that moment (re-read with cudaMemGetInfo at each
+ * admission, plus what the library's pool holds unused, minus reserve_bytes), so memory that other
+ * users of the GPU take or release after igp_server_create counts. A request that finds nothing
+ * running starts regardless and fails with IGP_E_NOMEM if the memory is not there. Requests are picked in submission order among those that may start. Resident graphs keep
  * their CSR and degree state on the device between requests (streaming, Alg. 2): an
  * IGP_REQ_APPEND request grows a resident graph by an edge increment and re-embeds it; requests
  * on the same graph_id run in submission order. The slots build or grow the requests' CSRs and
@@ -277,7 +283,7 @@ typedef struct igp_server_stats {
   int64_t submitted, completed, failed, cancelled, queued, running, resident_graphs;
   int64_t admitted_bytes;  /* estimated peak device bytes of the running requests */
   int64_t budget_bytes;    /* free device memory at igp_server_create minus reserve_bytes */
-  double latency_p50_s, latency_p99_s;  /* submit-to-done latency of completed requests */
+  double latency_p50_s, latency_p99_s;  /* submit-to-done latency of the last 65,536 completed requests */
   int64_t resident_bytes;  /* device bytes held by resident graphs */
   int64_t batches;         /* FFP launch sequences that served two or more requests together */
   int64_t batched;         /* requests embedded in such shared batches */
@@ -310,22 +316,25 @@ igp_status igp_server_release(igp_server* sv, int64_t graph_id);
 igp_status igp_server_get_stats(igp_server* sv, igp_server_stats* stats);
 
 /*
- * igp_embed without any memory allocation. (The paper has no counterpart: this serves callers that
- * may not allocate device memory at the moment they call, e.g. code recording a CUDA stream capture,
- * where cudaMalloc is not allowed, an allocator or memory-manager hook that must not re-enter the
- * CUDA allocator, or a loop that must keep a fixed memory footprint.)
+ * igp_embed without any memory allocation. (The paper has no counterpart.) Some callers cannot
+ * allocate device memory at the moment they call: an allocator or memory-manager hook, which would
+ * re-enter the allocator it is part of; a framework whose caching allocator already holds the free
+ * memory, so that a cudaMalloc of the library fails; a long-running loop that must keep a fixed
+ * memory footprint. For them this call allocates nothing: no cudaMalloc, cudaFree, pool or other
+ * allocating routine (igp_alloc_count does not move).
  *   row_ptr, col : DEVICE CSR of the graph, [N+1] and [row_ptr[N]] int32, in the form igp_graph_export
  *                  writes (symmetric, no self-loops, ids in [0, N)); it is trusted, not checked
- *   out          : DEVICE N x d fp32 output
+ *   out          : DEVICE (N - opts->out_row_begin) x d fp32 output (N x d with default options)
  *   tau, L, d, seed, opts : as for igp_embed; opts->profile and opts->chunk_cols must be 0
- * Same result as igp_embed on the graph built from that CSR. All temporaries live in a fixed
- * 16 MiB device array inside the library, reserved on every GPU that loads the library until the
- * process exits; sizes whose temporaries do not fit (about 2 N d storage-size bytes plus 8 N bytes
- * and 32 d bytes of column statistics) are rejected with IGP_E_INVAL before any GPU work. The call
- * issues no cudaMalloc, cudaFree or other allocating routine. The first call on each device looks
- * up that device's address of the array (cudaGetSymbolAddress); make it before any stream capture.
- * All calls share the array: calls whose GPU work overlaps (other streams, other threads) race, so
- * serialise them. Asynchronous on `stream`.
+ * Same result as igp_embed on the graph built from that CSR, to fp32 rounding (rows are taken in
+ * their own order, so the heaviest rows are summed in another order than igp_embed's).
+ * All temporaries live in a fixed 16 MiB device array inside the library, reserved on every GPU
+ * that loads the library until the process exits. Sizes whose temporaries do not fit (about
+ * 2 N d storage-size bytes plus 8 N bytes and 32 d bytes of column statistics) are rejected with
+ * IGP_E_INVAL before any GPU work. The first call on each device looks up that device's address
+ * of the array (cudaGetSymbolAddress); make that first call before any stream capture. All calls
+ * share the array, which keeps the last call's contents: calls whose GPU work overlaps (other
+ * streams, other threads) race, so serialise them. Asynchronous on `stream`.
  */
 igp_status igp_embed_noalloc(const int32_t* row_ptr, const int32_t* col, int32_t N, double tau, int32_t L, int32_t d,
                              uint64_t seed, float* out, const igp_embed_opts* opts, void* stream);

@@ -98,6 +98,7 @@ _SIGS = {
     "igp_version": (ctypes.c_char_p, []),
     "igp_last_error": (ctypes.c_char_p, []),
     "igp_launch_count": (ctypes.c_int64, []),
+    "igp_alloc_count": (ctypes.c_int64, []),
     "igp_embed_opts_init": (None, [ctypes.POINTER(EmbedOpts)]),
     "igp_graph_build": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
@@ -202,6 +203,11 @@ def version():
 
 def launch_count():
     return int(lib().igp_launch_count())
+
+
+def alloc_count():
+    """igp_alloc_count: memory allocations the library has made in this process."""
+    return int(lib().igp_alloc_count())
 
 
 def embed_opts(alpha=1.0, theta=0.1, eps=1e-3, x_scale=0.0, znorm_ddof=1, storage="f32", out_row_l2=False,

@@ -14,6 +14,9 @@ namespace igp {
 // ------------------------------------------------------------------ errors
 static thread_local char t_err[512] = "";
 static std::atomic<int64_t> g_launches{0};
+static std::atomic<int64_t> g_allocs{0};  // device and pinned-host allocations made by the library
+
+void count_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -75,6 +78,7 @@ igp_status dev_alloc(void** p, size_t bytes, cudaStream_t s) {
     set_error("cannot create the device memory pool");
     return IGP_E_CUDA;
   }
+  count_alloc();
   cudaError_t e = cudaMallocFromPoolAsync(p, bytes > 0 ? bytes : 1, pool, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -86,6 +90,18 @@ igp_status dev_alloc(void** p, size_t bytes, cudaStream_t s) {
 
 void dev_free(void* p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
+}
+
+size_t pool_idle_bytes() {
+  cudaMemPool_t pool = pool_for_current_device();
+  if (!pool) return 0;
+  uint64_t reserved = 0, used = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess ||
+      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return reserved > used ? (size_t)(reserved - used) : 0;
 }
 
 bool is_device_ptr(const void* p) {
@@ -185,6 +201,7 @@ extern "C" {
 const char* igp_version(void) { return "igp-gb300 0.1.0 (sm_103a)"; }
 const char* igp_last_error(void) { return t_err; }
 int64_t igp_launch_count(void) { return g_launches.load(); }
+int64_t igp_alloc_count(void) { return g_allocs.load(); }
 
 void igp_embed_opts_init(igp_embed_opts* o) {
   if (!o) return;
@@ -221,6 +238,7 @@ igp_status igp_graph_build_profiled(const int32_t* src, const int32_t* dst, int6
     return IGP_E_NOMEM;
   }
   cudaGetDevice(&g->device);
+  count_alloc();
   if (cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess ||
       cudaHostAlloc((void**)&g->err_host, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
     igp_status e = cuda_status(cudaGetLastError(), "graph handle set-up", __FILE__, __LINE__);

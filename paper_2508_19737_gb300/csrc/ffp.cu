@@ -2165,12 +2165,13 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
 // ============================================================================
 // igp_embed_noalloc: one FFP that allocates nothing.
 //
-// Some callers cannot allocate device memory while they call into this library:
-// code running inside a CUDA stream capture (cudaMalloc is not capturable), an
-// allocator hook or custom memory manager that must not re-enter the CUDA
-// allocator, or a real-time loop that has to keep a fixed memory footprint. This
-// entry point serves them: the caller passes the CSR, the output and a stream; all
-// temporaries live in one fixed device array that is part of the library image.
+// Some callers cannot allocate device memory while they call into this library: an
+// allocator hook or custom memory manager that must not re-enter the allocator it is
+// part of, a framework whose caching allocator already holds the free memory (so a
+// cudaMalloc here would fail), or a long-running loop that has to keep a fixed memory
+// footprint. This entry point serves them: the caller passes the CSR, the output and a
+// stream; all temporaries live in one fixed device array that is part of the library
+// image, and nothing here calls dev_alloc or any other allocating routine.
 //
 // The array below is reserved on every GPU that loads the library and stays
 // reserved until the process exits. Every call shares it, so calls whose GPU work

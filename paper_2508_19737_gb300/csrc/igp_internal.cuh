@@ -41,7 +41,11 @@ void count_launches(int64_t n);
 // cached (release threshold = max), so per-call workspaces cost no driver calls
 // after warm-up.
 igp_status dev_alloc(void** p, size_t bytes, cudaStream_t s);
+// Count one memory allocation (igp_alloc_count); dev_alloc counts its own.
+void count_alloc();
 void dev_free(void* p, cudaStream_t s);
+// Bytes the current device's library pool holds but does not use (free for dev_alloc).
+size_t pool_idle_bytes();
 bool is_device_ptr(const void* p);
 int num_sms();
 

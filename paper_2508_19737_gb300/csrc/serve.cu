@@ -63,7 +63,8 @@ struct igp_server {
   std::vector<std::thread> workers;
   std::vector<std::thread> batchers;
   std::deque<Req*> ready;           // CSR done, waiting for a batcher
-  std::vector<double> latencies;
+  std::vector<double> latencies;   // submit-to-done times of the last kLatencyWindow completions
+  size_t latency_next = 0;          // ring position once the window is full
   uint64_t next_ticket = 1;
   int64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, running = 0;
   int64_t batches = 0, batched = 0;  // shared FFP batches and the requests they served
@@ -71,6 +72,22 @@ struct igp_server {
 };
 
 namespace {
+
+constexpr size_t kLatencyWindow = 65536;
+
+// Device memory a new request may take right now: free device memory (re-read, so that memory
+// taken or released by other users of the GPU counts) plus what the library's pool holds
+// unused, less the reserve.
+size_t free_now(const igp_server* sv) {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const size_t avail = fr + igp::pool_idle_bytes();
+  const size_t res = (size_t)sv->opts.reserve_bytes;
+  return avail > res ? avail - res : 0;
+}
 
 // Device bytes a request may hold at its peak (edge copies, CSR build temporaries, the
 // CSR, per-node arrays, the two activation buffers and the output staging).
@@ -106,6 +123,8 @@ void set_resident(igp_server* sv, int64_t id, igp_graph* g) {
 // same resident graph is queued or running.
 Req* pick(igp_server* sv) {
   std::set<int64_t> seen;
+  size_t avail = 0;
+  bool avail_read = false;
   for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
     Req* q = *it;
     const bool on_graph = q->r.kind == IGP_REQ_APPEND || q->r.keep;
@@ -125,7 +144,14 @@ Req* pick(igp_server* sv) {
       return q;
     }
     q->est = estimate(sv, q->r);
-    if (sv->admitted + sv->resident_bytes + q->est > sv->budget && sv->running > 0) continue;  // wait for memory
+    if (sv->running > 0) {  // wait for memory: the server's budget, and the device's free memory now
+      if (sv->admitted + sv->resident_bytes + q->est > sv->budget) continue;
+      if (!avail_read) {
+        avail = free_now(sv);
+        avail_read = true;
+      }
+      if (q->est > avail) continue;
+    }
     sv->queue.erase(it);
     return q;
   }
@@ -319,7 +345,13 @@ void worker(igp_server* sv) {
       if (q->r.kind == IGP_REQ_APPEND || q->r.keep) sv->busy.erase(q->r.graph_id);
       if (q->status == IGP_OK) {
         sv->completed += 1;
-        sv->latencies.push_back(std::chrono::duration<double>(q->t_done - q->t_submit).count());
+        const double lat = std::chrono::duration<double>(q->t_done - q->t_submit).count();
+        if (sv->latencies.size() < kLatencyWindow) {
+          sv->latencies.push_back(lat);
+        } else {
+          sv->latencies[sv->latency_next] = lat;
+          sv->latency_next = (sv->latency_next + 1) % kLatencyWindow;
+        }
       } else {
         sv->failed += 1;
       }
