@@ -9,6 +9,12 @@ the directed CSR entries (twice the undirected edges).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference ...   # the FP64 oracle on the host cores
 
+The default run (the 2M-node workload, one GPU) also measures the other configurations and adds
+them as keys of the same JSON line: c2_f32 and c2_bf16 (the 200K-node graph, each with its own
+roofline), batched (512 uneven graphs in one batch against the same graphs one at a time in
+fp32) and served (the Poisson stream of snapshot requests: p50/p99 per snapshot and per graph,
+throughput against serial fp32). --no-extras skips them.
+
 Multi-GPU (torchrun): every rank runs an independent replica of the workload
 (the FFP of one graph does not shard); value = units of all ranks / max time.
 """
@@ -50,6 +56,9 @@ def parse():
     p.add_argument("--d", type=int, default=None, help="override the workload's embedding width")
     p.add_argument("--storage", default=None, choices=[None, "f32", "bf16"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="headline workload only (by default the 2M-node run also measures the 200K-node graph in "
+                        "both storages, the 512-graph batch and the served stream)")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--chunk-cols", type=int, default=0, help="columns per layer pass (0: automatic)")
     p.add_argument("--gather", default="auto", choices=["auto", "lsu", "bulk", "tma4"])
@@ -246,24 +255,27 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- batches
-def run_batch(args):
+def _batch_graph(args):
+    return synth.workload_batch_graph(*args)
+
+
+def draw_in_pool(fn, items):
+    """fn over items in a pool of spawned processes (spawned, so safe next to a CUDA context)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(fn, items, chunksize=4))
+
+
+def batch_measure(api, torch, name, storage, d, steps, warmup, local):
     """Many graphs embedded together (igp_batch_embed, CUDA-graph replay) against the same
     graphs embedded one after another in fp32 (igp_embed per graph). A step is one FFP of
-    every graph; the graphs are built and packed once, before timing."""
-    import torch
-
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2508_19737_gb300 import api
-
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    wl = synth.BATCH_WORKLOADS[args.workload]
-    storage = args.storage or wl["storage"]
+    every graph; the graphs are built and packed once, before timing. Returns the JSON dict."""
+    wl = synth.BATCH_WORKLOADS[name]
     sb = 2 if storage == "bf16" else 4
-    d = args.d or wl["d"]
     tau, L = wl["tau"], wl["L"]
-    gs = synth.workload_batch(args.workload)
+    G0 = wl["batch"]["G"]
+    gs = draw_in_pool(_batch_graph, [(name, k) for k in range(G0)])
     graphs = [api.graph_build(torch.from_numpy(g.src).cuda(), torch.from_numpy(g.dst).cuda(), g.N) for g in gs]
     batch = api.Batch(graphs)
     G, N, nnz, offs = batch.info()
@@ -271,7 +283,7 @@ def run_batch(args):
     out = torch.empty((N, d), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     opts = api.embed_opts(storage=storage)
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         batch.embed(tau, L, d, seeds, out=out, opts=opts, stream=stream)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
@@ -281,7 +293,7 @@ def run_batch(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         batch.embed(tau, L, d, seeds, out=out, opts=opts, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -289,7 +301,7 @@ def run_batch(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     units = float(nnz) * d * L
-    value = units * args.steps / (ms / 1e3)
+    value = units * steps / (ms / 1e3)
     # per-launch layer time (plain launches with events)
     prof = api.Profile()
     popts = api.embed_opts(storage=storage, profile=prof)
@@ -316,51 +328,31 @@ def run_batch(args):
     seq_ms = e0.elapsed_time(e1) / reps
     seq_value = units / (seq_ms / 1e3)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warmup,
+        "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": storage, "data": "synthetic",
-        "config": {"workload": args.workload, **wl["batch"], "N_total": N, "nnz_total": int(nnz), "d": d,
+        "config": {"workload": name, **wl["batch"], "N_total": N, "nnz_total": int(nnz), "d": d,
                    "tau": tau, "L": L, "storage": storage, "accumulate": "f32",
                    "step": "igp_batch_embed of all graphs (CUDA-graph replay); graphs built and packed once",
                    "l2": "inputs larger than L2" if N * d * sb > L2_BYTES else "working set may fit L2"},
         "roofline": {"bound": "hbm", "achieved": lb / layer_s / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": lb / layer_s / 1e9 / peak, "traffic": None, "kernel": "k_layer_batch",
-                     "avg_launch_ms": layer_s * 1e3, "algorithmic_bytes_per_launch": lb},
+                     "avg_launch_ms": layer_s * 1e3, "algorithmic_bytes_per_launch": lb,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else
+                     "fallback 6800 GB/s"},
         "sequential_fp32": {"value": seq_value, "unit": UNIT, "ms_per_pass": seq_ms,
                             "what": "igp_embed of each graph in turn, fp32 storage, same d, tau, L, seeds"},
         "speedup_vs_sequential_fp32": value / seq_value,
         "gpu_launches": int(launches),
         "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
     batch.free()
-    return 0
+    for g in graphs:
+        g.free()
+    return line
 
 
-def _serve_graph(args):
-    return synth.serve_graph(*args)
-
-
-def run_serve(args):
-    """The served stream: snapshot requests (an edge increment of one graph, then the FFP of
-    the whole graph so far) arriving as a Poisson process, handled by igp_server (concurrent
-    slots, admission by free device memory, resident graphs). Reported: latency p50/p99 per
-    snapshot and per graph under the stream's arrival rate; the server's throughput with every
-    request queued at once; and the same requests handled one at a time by direct library
-    calls in fp32 storage (and in the served storage). Edges come from host memory and every
-    result is copied to host memory inside the timed regions."""
-    import concurrent.futures as cf
-    import multiprocessing as mp
-
-    wl = synth.SERVE_WORKLOADS[args.workload]
-    params = wl["stream"]
-    storage = args.storage or wl["storage"]
-    d, tau, L = args.d or wl["d"], wl["tau"], wl["L"]
-    G, T = params["G"], params["T"]
-    # graphs are drawn in a spawn pool before the first CUDA call
-    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
-        incs = list(ex.map(_serve_graph, [(params, k) for k in range(G)]))
-    times, order = synth.serve_schedule(params)
+def run_batch(args):
     import torch
 
     import __graft_entry__
@@ -369,6 +361,31 @@ def run_serve(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    wl = synth.BATCH_WORKLOADS[args.workload]
+    line = batch_measure(api, torch, args.workload, args.storage or wl["storage"], args.d or wl["d"], args.steps,
+                         args.warmup, local)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _serve_graph(args):
+    return synth.serve_graph(*args)
+
+
+def serve_measure(api, torch, name, storage, d, slots, batch_rows, warmup, local):
+    """The served stream: snapshot requests (an edge increment of one graph, then the FFP of
+    the whole graph so far) arriving as a Poisson process, handled by igp_server (concurrent
+    slots, admission by free device memory, resident graphs). Reported: latency p50/p99 per
+    snapshot and per graph under the stream's arrival rate; the server's throughput with every
+    request queued at once; and the same requests handled one at a time by direct library
+    calls in fp32 storage (and in the served storage). Edges come from host memory and every
+    result is copied to host memory inside the timed regions. Returns the JSON dict."""
+    wl = synth.SERVE_WORKLOADS[name]
+    params = wl["stream"]
+    tau, L = wl["tau"], wl["L"]
+    G, T = params["G"], params["T"]
+    incs = draw_in_pool(_serve_graph, [(params, k) for k in range(G)])
+    times, order = synth.serve_schedule(params)
     R = len(order)
     nfinal = [inc[-1][2] for inc in incs]
     outs = [torch.empty((n, d), dtype=torch.float32, pin_memory=True) for n in nfinal]
@@ -391,11 +408,10 @@ def run_serve(args):
         return sv.submit(s_, d_, n_, tau, L, d, seed, kind="embed" if t == 0 else "append", graph_id=k,
                          keep=(t == 0), out=outs[k], storage=st)
 
-    slots = args.slots
     # warm-up: a few requests of the smallest graph
     kmin = int(np.argmin(nfinal))
-    sv = api.Server(slots=slots, batch_rows=args.batch_rows)
-    for _ in range(max(args.warmup, 3)):
+    sv = api.Server(slots=slots, batch_rows=batch_rows)
+    for _ in range(max(warmup, 3)):
         sv.wait(submit(sv, kmin, 0, storage, 0))
     sv.close()
 
@@ -403,7 +419,7 @@ def run_serve(args):
     clocks = ClockSampler(local)
     clocks.start()
     n0 = api.launch_count()
-    sv = api.Server(slots=slots, batch_rows=args.batch_rows)
+    sv = api.Server(slots=slots, batch_rows=batch_rows)
     tickets = [None] * R
     t0 = time.perf_counter()
     for r, (k, t) in enumerate(order):
@@ -424,7 +440,7 @@ def run_serve(args):
     sv.close()
 
     # (2) saturation: every request queued at once, same order
-    sv = api.Server(slots=slots, batch_rows=args.batch_rows)
+    sv = api.Server(slots=slots, batch_rows=batch_rows)
     t0 = time.perf_counter()
     tickets = [submit(sv, k, t, storage, 1000 * k + t) for k, t in order]
     for tk in tickets:
@@ -452,12 +468,12 @@ def run_serve(args):
     t_ser32 = serial("f32")
     t_ser = serial(storage)
     pct = lambda v, q: float(np.percentile(np.asarray(v), q))  # noqa: E731
-    line = {
+    return {
         "metric": "served snapshot requests/s", "value": R / t_sat, "unit": "requests/s", "n_gpus": 1,
-        "steps": R, "warmup": max(args.warmup, 3), "ms_per_step": t_sat / R * 1e3, "higher_is_better": True,
+        "steps": R, "warmup": max(warmup, 3), "ms_per_step": t_sat / R * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
-        "config": {"workload": args.workload, **params, "d": d, "tau": tau, "L": L, "storage": storage,
-                   "slots": slots, "batch_rows": args.batch_rows, "requests": R, "N_total_final": int(sum(nfinal)),
+        "config": {"workload": name, **params, "d": d, "tau": tau, "L": L, "storage": storage,
+                   "slots": slots, "batch_rows": batch_rows, "requests": R, "N_total_final": int(sum(nfinal)),
                    "step": "one snapshot request: increment merge (or CSR build) + FFP + result to host",
                    "l2": "per-request working sets up to the largest graph; not flushed between requests"},
         "edge_dim_layer_per_s": units / t_sat,
@@ -473,11 +489,148 @@ def run_serve(args):
         "gpu_launches": int(launches_open),
         "clocks": clk,
     }
+
+
+def run_serve(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_19737_gb300 import api
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    wl = synth.SERVE_WORKLOADS[args.workload]
+    line = serve_measure(api, torch, args.workload, args.storage or wl["storage"], args.d or wl["d"], args.slots,
+                         args.batch_rows, args.warmup, local)
     print(json.dumps(line), flush=True)
     return 0
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def single_measure(api, torch, name, storage, steps, warmup, local, world=1, chunk_cols=0, gather="auto",
+                   g=None, barrier=lambda: None):
+    """Whole steps (CSR build from the device-resident edge list + Eq. 1 factors + Theta + L
+    layers + output) of one single-graph workload, timed with CUDA events on the launching
+    stream after warm-up; per-phase device times from the library's profile; clocks sampled
+    during the timed region. Returns (dict, context for the end-to-end run)."""
+    wl = synth.WORKLOADS[name]
+    sb = 2 if storage == "bf16" else 4
+    d, tau, L = wl["d"], wl["tau"], wl["L"]
+    if g is None:
+        g = synth.workload_graph(name)
+    N, M = g.N, g.M
+    src = torch.from_numpy(g.src).cuda()
+    dst = torch.from_numpy(g.dst).cuda()
+    out = torch.empty((N, d), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    opts = api.embed_opts(storage=storage, chunk_cols=chunk_cols, gather=gather)
+    probe = api.graph_build(src, dst, N)
+    _, nnz, maxdeg = probe.info()
+    probe.free()
+
+    def step(prof=None):
+        gr = api.graph_build(src, dst, N, stream=stream, profile=prof)
+        opts.profile = prof.handle if prof is not None else None
+        api.embed(gr, tau, L, d, 0, out=out, opts=opts, stream=stream)
+        gr.free()
+
+    for _ in range(max(warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    prof = api.Profile()
+    n0 = api.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        step(prof)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = api.launch_count() - n0
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    phases = prof.read()
+    prof.close()
+    opts.profile = None
+    units_step = float(nnz) * d * L
+    layer_ms, layer_n = phases["layer"]
+    avg_layer_s = layer_ms / max(layer_n, 1) / 1e3
+    lb = layer_bytes(N, nnz, d, sb)
+    peak, peak_src = peaks()
+    achieved = lb / avg_layer_s / 1e9
+    ffp_ms = sum(phases[k][0] for k in ("dinv", "theta", "layer", "output")) / steps
+    res = {
+        "value": replica_rate(units_step, steps, world, ms), "unit": UNIT, "ms_per_step": ms / steps,
+        "units_per_step": units_step, "dtype": storage,
+        "config": {"workload": name, **wl["graph"], "M_drawn": M, "nnz": int(nnz), "max_deg": int(maxdeg),
+                   "d": d, "tau": tau, "L": L, "storage": storage, "accumulate": "f32",
+                   "chunk_cols": chunk_cols or "auto", "gather": gather,
+                   "l2": "inputs larger than L2 (edge list %d MB, T %d MB each > 129 MB)" % (
+                       8 * M >> 20, N * d * sb >> 20) if N * d * sb > L2_BYTES else
+                   "working set may fit L2 (inputs not flushed between steps)"},
+        "phase_ms_per_step": {k: v[0] / steps for k, v in phases.items()},
+        "ffp_only": {"value": units_step / (ffp_ms / 1e3), "unit": UNIT,
+                     "what": "dinv + theta + L layers + output, CSR build excluded"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": recorded_traffic(name, storage), "kernel": "k_layer",
+                     "algorithmic_bytes_per_launch": lb, "avg_launch_ms": avg_layer_s * 1e3,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else
+                     "fallback 6800 GB/s"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    return res, dict(g=g, opts=opts, stream=stream, N=N, M=M, d=d, tau=tau, L=L, units_step=units_step, wl=wl)
+
+
+def e2e_measure(api, torch, ctx, steps, world, barrier=lambda: None):
+    """The same step through the public API with pinned host edges in and pinned host
+    embeddings out (host<->device copies inside the timed region)."""
+    g, opts, stream, N, d = ctx["g"], ctx["opts"], ctx["stream"], ctx["N"], ctx["d"]
+    src_h = torch.from_numpy(g.src).pin_memory()
+    dst_h = torch.from_numpy(g.dst).pin_memory()
+    out_h = torch.empty((N, d), dtype=torch.float32).pin_memory()
+
+    def step_e2e():
+        gr = api.graph_build(src_h, dst_h, N, stream=stream)
+        api.embed(gr, ctx["tau"], ctx["L"], d, 0, out=out_h, opts=opts, stream=stream)
+        gr.free()
+    step_e2e()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    return {"value": replica_rate(ctx["units_step"], steps, world, e2e_s * 1e3), "unit": UNIT,
+            "h2d_bytes_per_step": 2 * 4 * ctx["M"], "d2h_bytes_per_step": N * d * 4, "steps": steps}
+
+
+def extras(api, torch, args, local):
+    """The other configurations, measured in the same run as the headline: the 200K-node graph
+    in both storages, the 512-graph batch and the served stream (keys of the headline line)."""
+    out = {}
+    for storage in ("f32", "bf16"):
+        r, _ = single_measure(api, torch, "dcsbm-200k", storage, 20, 3, local)
+        out[f"c2_{storage}"] = r
+    wl = synth.BATCH_WORKLOADS["dcsbm-batch512"]
+    out["batched"] = batch_measure(api, torch, "dcsbm-batch512", wl["storage"], wl["d"], 5, 3, local)
+    wl = synth.SERVE_WORKLOADS["dcsbm-serve"]
+    out["served"] = serve_measure(api, torch, "dcsbm-serve", wl["storage"], wl["d"], args.slots, args.batch_rows,
+                                  3, local)
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -497,125 +650,40 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    wl = synth.WORKLOADS[args.workload]
-    storage = args.storage or wl["storage"]
-    sb = 2 if storage == "bf16" else 4
-    d, tau, L = wl["d"], wl["tau"], wl["L"]
-    g = synth.workload_graph(args.workload)
-    N, M = g.N, g.M
-    src = torch.from_numpy(g.src).cuda()
-    dst = torch.from_numpy(g.dst).cuda()
-    out = torch.empty((N, d), dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-    opts = api.embed_opts(storage=storage, chunk_cols=args.chunk_cols, gather=args.gather)
-    probe = api.graph_build(src, dst, N)
-    _, nnz, maxdeg = probe.info()
-    probe.free()
-
-    def step(prof=None):
-        gr = api.graph_build(src, dst, N, stream=stream, profile=prof)
-        opts.profile = prof.handle if prof is not None else None
-        api.embed(gr, tau, L, d, 0, out=out, opts=opts, stream=stream)
-        gr.free()
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    prof = api.Profile()
-    n0 = api.launch_count()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        step(prof)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    launches = api.launch_count() - n0
-    clk = clocks.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1), world)
-    phases = prof.read()
-    prof.close()
-    ms_step = ms / args.steps
-    units_step = float(nnz) * d * L
-    value = replica_rate(units_step, args.steps, world, ms)
-
-    # end to end through the public API: pinned host edges in, pinned host embeddings out
-    src_h = torch.from_numpy(g.src).pin_memory()
-    dst_h = torch.from_numpy(g.dst).pin_memory()
-    out_h = torch.empty((N, d), dtype=torch.float32).pin_memory()
-    e2e_steps = args.e2e_steps or max(3, min(args.steps, 20))
-
-    def step_e2e():
-        gr = api.graph_build(src_h, dst_h, N, stream=stream)
-        api.embed(gr, tau, L, d, 0, out=out_h, opts=opts, stream=stream)
-        gr.free()
-    opts.profile = None
-    step_e2e()
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        step_e2e()
-    torch.cuda.synchronize()
-    barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    e2e_value = replica_rate(units_step, e2e_steps, world, e2e_s * 1e3)
-
+    wl = synth.WORKLOADS[args.workload]
+    storage = args.storage or wl["storage"]
+    res, ctx = single_measure(api, torch, args.workload, storage, args.steps, args.warmup, local, world,
+                              args.chunk_cols, args.gather, barrier=barrier)
+    e2e = e2e_measure(api, torch, ctx, args.e2e_steps or max(3, min(args.steps, 20)), world, barrier)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
-
-    layer_ms, layer_n = phases["layer"]
-    avg_layer_s = layer_ms / max(layer_n, 1) / 1e3
-    lb = layer_bytes(N, nnz, d, sb)
-    peak, peak_src = peaks()
-    achieved = lb / avg_layer_s / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(args.workload, storage), "kernel": "k_layer",
-                "algorithmic_bytes_per_launch": lb, "avg_launch_ms": avg_layer_s * 1e3,
-                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else
-                "fallback 6800 GB/s"}
-    ffp_ms = sum(phases[k][0] for k in ("dinv", "theta", "layer", "output")) / args.steps
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        smp = OracleSample(g, wl, 10.0)
+        smp = OracleSample(ctx["g"], wl, 10.0)
         rate, dt = smp.rate()
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": smp.describe(dt)}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": storage, "data": "synthetic",
-        "config": {"workload": args.workload, **wl["graph"], "M_drawn": M, "nnz": int(nnz), "max_deg": int(maxdeg),
-                   "d": d, "tau": tau, "L": L, "storage": storage, "accumulate": "f32",
-                   "chunk_cols": args.chunk_cols or "auto",
-                   "gather": args.gather,
-                   "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (edge list %d MB, T %d MB each > 129 MB)" % (
-                       8 * M >> 20, N * d * sb >> 20) if N * d * sb > L2_BYTES else "working set may fit L2"},
-        "phase_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
-        "ffp_only": {"value": units_step / (ffp_ms / 1e3), "unit": UNIT,
-                     "what": "dinv + theta + L layers + output, CSR build excluded"},
-        "roofline": roofline,
+        "config": {**res["config"], "parallelism": f"replicas{world}"},
+        "phase_ms_per_step": res["phase_ms_per_step"],
+        "ffp_only": res["ffp_only"],
+        "roofline": res["roofline"],
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 4 * M, "d2h_bytes_per_step": N * d * 4,
-                "steps": e2e_steps},
-        "gpu_launches": int(launches),
-        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": res["gpu_launches"],
+        "clocks": res["clocks"],
     }
+    if world == 1 and not args.no_extras and args.workload == "dcsbm-2m" and args.storage is None:
+        line.update(extras(api, torch, args, local))
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

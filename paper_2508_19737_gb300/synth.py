@@ -82,8 +82,10 @@ def block_sizes(rng, N, B, dirichlet_alpha=None):
 
 
 def dcsbm(N, B, mean_deg, gamma, ratio, seed=0, dirichlet_alpha=None, order="random",
-          theta_range=(1.0, 100.0)):
-    """Draw one DC-SBM graph (see the module docstring)."""
+          theta_range=(1.0, 100.0), intra_fraction=None):
+    """Draw one DC-SBM graph (see the module docstring). With intra_fraction, `ratio` is ignored
+    and the per-pair ratio r is solved from the drawn block masses Tb so that the expected share
+    of within-block edge draws is intra_fraction: r sum Tb^2 / (r sum Tb^2 + Ttot^2 - sum Tb^2)."""
     rng = np.random.default_rng(seed)
     sizes = block_sizes(rng, N, B, dirichlet_alpha)
     starts = np.concatenate([[0], np.cumsum(sizes)])
@@ -93,6 +95,10 @@ def dcsbm(N, B, mean_deg, gamma, ratio, seed=0, dirichlet_alpha=None, order="ran
     Tb = cum[starts[1:]] - cum[starts[:-1]]
     Ttot = cum[-1]
     M = int(round(N * mean_deg / 2.0))
+    if intra_fraction is not None:
+        S2 = float((Tb * Tb).sum())
+        f = float(intra_fraction)
+        ratio = f * (Ttot * Ttot - S2) / ((1.0 - f) * S2)
 
     # u with weight theta_u * (ratio*Tb + Ttot - Tb)
     wu = th * (ratio * Tb[blk] + Ttot - Tb[blk])
@@ -134,9 +140,40 @@ def dcsbm(N, B, mean_deg, gamma, ratio, seed=0, dirichlet_alpha=None, order="ran
     blocks[label] = blk
     theta_l = np.empty(N)
     theta_l[label] = th
-    params = dict(N=N, B=B, mean_deg=mean_deg, gamma=gamma, ratio=ratio,
-                  dirichlet_alpha=dirichlet_alpha, order=order)
+    params = dict(N=N, B=B, mean_deg=mean_deg, gamma=gamma, ratio=float(ratio),
+                  dirichlet_alpha=dirichlet_alpha, order=order, intra_fraction=intra_fraction)
     return DCSBM(src, dst, N, blocks, theta_l, seed, params)
+
+
+# Blocks of the paper's benchmark graphs per N (Table I) and InfraredGP's settings (tau, L, d)
+# per N (Table II), static and streaming.
+TABLE1_BLOCKS = {5_000: 19, 10_000: 25, 50_000: 44, 100_000: 56, 500_000: 98, 1_000_000: 125}
+TABLE2_STATIC = {5_000: (-6.0, 10, 64), 10_000: (-3.0, 9, 64), 50_000: (-80.0, 40, 32),
+                 100_000: (-80.0, 60, 32), 500_000: (-80.0, 70, 32), 1_000_000: (-80.0, 60, 32)}
+TABLE2_STREAMING = {100_000: (-100.0, 20, 32), 1_000_000: (-100.0, 20, 16)}
+
+
+def challenge_like(N, K=None, seed=0, mean_deg=40.0, count_ratio=2.5, dirichlet_alpha=2.0):
+    """A DC-SBM shaped like the benchmark graphs of the paper's experiments (Sec. IV-A, Table I):
+    K blocks (Table I's count for N by default) of Dirichlet(2) sizes, mean degree 40, degree
+    propensities from a power law of exponent 1.5 on [1, 12] (degrees roughly 10-140 around the
+    mean, like Table I's spread), and about count_ratio within-block edges per between-block edge
+    (the benchmark's 2.5), i.e. an expected within-block share of edge draws of
+    count_ratio / (count_ratio + 1)."""
+    if K is None:
+        K = TABLE1_BLOCKS.get(N, max(2, int(round(N ** 0.4))))
+    return dcsbm(N, K, mean_deg, 1.5, 1.0, seed=seed, dirichlet_alpha=dirichlet_alpha, theta_range=(1.0, 12.0),
+                 intra_fraction=count_ratio / (count_ratio + 1.0))
+
+
+def gaussian_input(seed, N, d, x_scale=None):
+    """A seeded N x d fp64 Gaussian matrix, N(0, 1) times x_scale (1/sqrt(d) by default: the
+    N(0, 1/d) random input of Alg. 1), drawn on the host with numpy's PCG64. Tests feed it to the
+    GPU (as igp_embed_opts.x_in, in the storage type) and to the oracle alike, so that both start
+    from the same values."""
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), int(N), int(d), 0x7E7A]))
+    xs = 1.0 / np.sqrt(d) if x_scale is None else float(x_scale)
+    return rng.standard_normal((N, d)) * xs
 
 
 def log_uniform_sizes(rng, n, lo, hi):

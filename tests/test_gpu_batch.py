@@ -6,6 +6,7 @@ import pytest
 
 import oracle
 from paper_2508_19737_gb300 import synth
+from tests.checks import check_bf16
 
 pytestmark = pytest.mark.gpu
 
@@ -105,56 +106,11 @@ def test_batch_host_output_and_options(api):
 
 
 
-def _row_errs(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
-
-
-def _kmeans_labels(E, k, seed=0, iters=40):
-    """Lloyd's k-means from k rows chosen by a seeded generator. The same rows start every
-    embedding of a graph, so two nearly equal embeddings start from nearly equal centres."""
-    E = np.asarray(E, dtype=np.float64)
-    rng = np.random.default_rng(seed)
-    C = E[rng.choice(len(E), size=k, replace=False)].copy()
-    e2 = (E * E).sum(1)[:, None]
-    lab = np.zeros(len(E), dtype=np.int64)
-    for _ in range(iters):
-        lab = np.argmin(e2 - 2.0 * E @ C.T + (C * C).sum(1)[None, :], axis=1)
-        cnt = np.bincount(lab, minlength=k)
-        S = np.zeros_like(C)
-        np.add.at(S, lab, E)
-        nz = cnt > 0
-        C[nz] = S[nz] / cnt[nz, None]
-    return lab
-
-
 def check_bf16_against_oracles(got, g, seed, d, tau, L):
-    """bf16 storage against the oracle, three ways. (1) The kernel does what the storage
-    specifies: within 5e-3 of the bf16-emulating oracle on every row. (2) Against FP64, 99.9 %
-    of rows are within 2e-2, and every row is within 5e-3 of the error that the storage alone
-    causes (the emulation's own error). Where tau < 0 gives low-degree nodes layer gains above 1
-    (Eq. 1, Fig. 1), the rounding of Theta and of each T^(l) grows geometrically with L on a
-    few rows, and no bf16 storage keeps those rows within 2e-2. (3) On graphs of 5,000 nodes or
-    more, k-means with the planted number of blocks reaches an NMI against the planted partition
-    within 0.01 of the FP64 embedding's. On smaller graphs k-means alone moves the NMI by more
-    than that."""
-    from paper_2508_19737_gb300 import metrics
+    """The bf16 checks of tests/checks.py on graph g with the Theta of `seed` (the oracle draws
+    it from the same counter-based generator as the device)."""
     rp, col = oracle.build_csr(g.src, g.dst, g.N)
-    X = oracle.theta_input(seed, g.N, d)
-    ref = oracle.ffp(rp, col, X, tau, L)
-    emu = oracle.ffp(rp, col, X, tau, L, storage="bf16")
-    e_emu = _row_errs(got, emu)
-    e_ref = _row_errs(got, ref)
-    e_store = _row_errs(emu, ref)
-    assert e_emu.max() <= 5e-3, ("kernel vs bf16 storage", float(e_emu.max()))
-    assert np.quantile(e_ref, 0.999) <= TOL["bf16"], ("99.9 % of rows", float(np.quantile(e_ref, 0.999)))
-    assert np.all(e_ref <= e_store + 5e-3), ("beyond the storage's own error", float((e_ref - e_store).max()))
-    if g.N >= 5000:
-        B = int(np.max(g.blocks)) + 1
-        n_ref = metrics.nmi(g.blocks, _kmeans_labels(ref, B))
-        n_got = metrics.nmi(g.blocks, _kmeans_labels(got, B))
-        assert abs(n_got - n_ref) <= 0.01, ("NMI", n_got, n_ref)
+    return check_bf16(got, rp, col, oracle.theta_input(seed, g.N, d), tau, L, blocks=g.blocks)
 
 
 def test_batch512_full_size_sampled(api):

@@ -263,50 +263,7 @@ def test_deterministic_and_stream_ordered(api):
     assert np.array_equal(outs[0], outs[1])
 
 
-# ---------------------------------------------------------------------------- workloads
-def test_200k_config_parity_both_storages(api):
-    wl = synth.WORKLOADS["dcsbm-200k"]
-    g = synth.workload_graph("dcsbm-200k")
-    import torch
-    gr = api.graph_build(_dev(g.src), _dev(g.dst), g.N)
-    rp, col = oracle.build_csr(g.src, g.dst, g.N)
-    X = oracle.theta_input(0, g.N, wl["d"])
-    ref = oracle.ffp(rp, col, X, wl["tau"], wl["L"])
-    for storage in ("f32", "bf16"):
-        out = torch.empty((g.N, wl["d"]), dtype=torch.float32, device="cuda")
-        api.embed(gr, wl["tau"], wl["L"], wl["d"], 0, out=out, storage=storage)
-        assert row_rel_err(out.cpu().numpy(), ref) <= TOL[storage]
-    gr.free()
-
-
-def test_2m_config_full_size(api):
-    """The 2M-node workload in the configuration the benchmark times: bit-exact CSR and
-    degree factors, one and two full layers against the oracle, and properties of the
-    full 10-layer output (logits have column mean 0 and sample std 1)."""
-    import torch
-    wl = synth.WORKLOADS["dcsbm-2m"]
-    g = synth.workload_graph("dcsbm-2m")
-    gr = api.graph_build(_dev(g.src), _dev(g.dst), g.N)
-    rp, col = oracle.build_csr(g.src, g.dst, g.N)
-    rpg, colg = gr.export()
-    assert np.array_equal(rpg, rp) and np.array_equal(colg, col)
-    del colg
-    ref_dinv = oracle.inv_sqrt_degrees(oracle.degree_correction(oracle.degrees(rp), wl["tau"])).astype(np.float32)
-    assert np.array_equal(api.degree_factors(gr, wl["tau"]).view(np.uint32), ref_dinv.view(np.uint32))
-    d = wl["d"]
-    X = oracle.theta_input(0, g.N, d)
-    out = torch.empty((g.N, d), dtype=torch.float32, device="cuda")
-    for L in (1, 2):
-        ref = oracle.ffp(rp, col, X, wl["tau"], L)
-        api.embed(gr, wl["tau"], L, d, 0, out=out, storage=wl["storage"])
-        assert row_rel_err(out.cpu().numpy(), ref) <= TOL[wl["storage"]]
-    api.embed(gr, wl["tau"], wl["L"], d, 0, out=out, storage=wl["storage"])
-    z = out.double()
-    z = torch.log(z) - torch.log1p(-z)
-    assert torch.isfinite(z).all()
-    assert float(z.mean(0).abs().max()) < 1e-2
-    assert float((z.std(0) - 1).abs().max()) < 2e-2
-    gr.free()
+# The named workloads at full size and depth: tests/test_gpu_workloads.py
 
 
 # ---------------------------------------------------------------------------- gather modes
