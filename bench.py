@@ -49,7 +49,8 @@ def parse():
     p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="dcsbm-2m", choices=sorted(synth.WORKLOADS) + sorted(synth.BATCH_WORKLOADS) + sorted(synth.SERVE_WORKLOADS))
+    p.add_argument("--workload", default="dcsbm-2m", choices=sorted(synth.WORKLOADS) + sorted(synth.BATCH_WORKLOADS)
+                   + sorted(synth.SERVE_WORKLOADS) + sorted(synth.STREAM_WORKLOADS))
     p.add_argument("--slots", type=int, default=8, help="concurrent requests of the served stream")
     p.add_argument("--batch-rows", type=int, default=0,
                    help="served graphs with fewer nodes share batched FFPs (0: every slot embeds its own)")
@@ -507,6 +508,84 @@ def run_serve(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- streaming (Alg. 2)
+def stream_measure(api, torch, name, local):
+    """Alg. 2 against Alg. 1 re-run from scratch at every step (the comparison of Figs. 2-3): a
+    graph shaped like the paper's benchmark graphs arrives as 10 snowball increments. Streaming:
+    each step merges the increment into the resident CSR, runs the FFP over all nodes so far,
+    extracts the new nodes' rows, fits the device clusterer on them and assigns every node so
+    far (the clustering of a step overlaps the next step's FFP). Static: each step builds the
+    cumulative graph, runs the FFP over all nodes, fits a fresh clusterer on every row and
+    assigns them. Per step: seconds of each and the NMI / pairwise F1 of its partition against
+    the planted blocks of the nodes so far. Returns the JSON dict."""
+    from paper_2508_19737_gb300 import metrics, stream
+    wl = synth.STREAM_WORKLOADS[name]
+    g = synth.challenge_like(wl["N"], seed=wl["seed"])
+    incs, order = synth.split_increments(g, wl["T"], "snowball", seed=wl["seed"], return_order=True)
+    blocks = g.blocks[order]
+    tau, L, d, storage = wl["tau"], wl["L"], wl["d"], wl["storage"]
+    T_cl, B_cl = wl["threshold"], wl["batch"]
+
+    def make():
+        return api.Clusterer(d, T_cl, batch=B_cl)
+
+    def quality(lab, n):
+        return metrics.nmi(blocks[:n], lab), metrics.pairwise_scores(blocks[:n], lab)[2]
+    # warm-up (kernels loaded, pools grown)
+    with stream.StreamingPartitioner(make(), tau=tau, L=L, d=d, seed=0, storage=storage) as sp:
+        sp.step(*incs[0])
+        sp.labels(0)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    with stream.StreamingPartitioner(make(), tau=tau, L=L, d=d, seed=0, storage=storage) as sp:
+        for s_, d_, n_ in incs:
+            sp.step(s_, d_, n_)
+        labs = [sp.labels(t) for t in range(len(incs))]
+        t_stream = time.perf_counter() - t0
+        timings = [sp.timings[t] for t in range(len(incs))]
+    st_rows = []
+    for t, (s_, d_, n_) in enumerate(incs):
+        st_rows.append({"N_t": n_, "ffp_s": timings[t]["ffp_s"], "cluster_s": timings[t]["cluster_s"],
+                        **dict(zip(("nmi", "f1"), quality(labs[t], n_)))})
+    # static re-runs on the cumulative graph of every step
+    static_rows = []
+    t_static = 0.0
+    for t in range(len(incs)):
+        src = np.concatenate([incs[k][0] for k in range(t + 1)])
+        dst = np.concatenate([incs[k][1] for k in range(t + 1)])
+        n_ = incs[t][2]
+        cl = make()
+        t1 = time.perf_counter()
+        lab, ffp_s, cl_s = stream.static_partition(src, dst, n_, cl, tau=tau, L=L, d=d, seed=t, storage=storage)
+        t_static += time.perf_counter() - t1
+        cl.free()
+        static_rows.append({"N_t": n_, "ffp_s": ffp_s, "cluster_s": cl_s, **dict(zip(("nmi", "f1"), quality(lab, n_)))})
+    clk = clocks.stop()
+    return {
+        "what": "Alg. 2 (merge, FFP, new rows, device clusterer fit + assign, clustering overlapped with the next "
+                "FFP) against Alg. 1 from scratch at every step, on the same increments",
+        "config": {"workload": name, **{k: v for k, v in wl.items()}, "blocks": int(blocks.max()) + 1,
+                   "clusterer": "device BIRCH leaf level (igp_clusterer)"},
+        "streaming_total_s": t_stream, "static_total_s": t_static, "speedup": t_static / t_stream,
+        "streaming_steps": st_rows, "static_steps": static_rows, "clocks": clk,
+    }
+
+
+def run_stream(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_19737_gb300 import api
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    print(json.dumps(stream_measure(api, torch, args.workload, local)), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def single_measure(api, torch, name, storage, steps, warmup, local, world=1, chunk_cols=0, gather="auto",
                    g=None, barrier=lambda: None):
@@ -635,6 +714,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in synth.STREAM_WORKLOADS:
+        return 0 if dist_env()[0] != 0 else run_stream(args)
     if args.workload in synth.BATCH_WORKLOADS or args.workload in synth.SERVE_WORKLOADS:
         if dist_env()[0] != 0:  # one process runs these modes; other ranks have nothing to do
             return 0

@@ -153,6 +153,21 @@ igp_status igp_graph_info(const igp_graph* g, int32_t* N, int64_t* nnz, int32_t*
 /* Copy the CSR out: row_ptr[N+1] and col[nnz] (host or device; either may be NULL). */
 igp_status igp_graph_export(const igp_graph* g, int32_t* row_ptr, int32_t* col, void* stream);
 
+/*
+ * A graph from its CSR (the form igp_graph_export writes: the symmetric adjacency of Sec. II, no
+ * self-loops, every row's columns sorted increasingly without repeats), e.g. to restore a graph
+ * saved with igp_graph_export without its edge list.
+ *   row_ptr : N+1 int32 (host or device), row_ptr[0] = 0, row_ptr[N] = nnz
+ *   col     : nnz int32 (host or device)
+ *   validate: 1 = check all of the above on the device (each entry's mirror by binary search;
+ *             O(nnz log(max degree))); 0 = trust the input (a CSR that breaks them gives
+ *             undefined embeddings, but no out-of-bounds access as long as row_ptr is valid)
+ * Both arrays are copied. Errors: IGP_E_INVAL (bad sizes, or a check failed: no handle is
+ * created; the message names the broken property), IGP_E_NOMEM, IGP_E_CUDA. Synchronises `stream`.
+ */
+igp_status igp_graph_import(const int32_t* row_ptr, const int32_t* col, int32_t N, int64_t nnz, int32_t validate,
+                            void* stream, igp_graph** out);
+
 /* Eq. 1 degree factors D_tau^{-1/2} as fp32 (computed in fp64, IEEE sqrt and division, then
  * rounded to nearest fp32), dinv[N] host or device. 0 where D_tau == 0 (tau = 0, isolated node). */
 igp_status igp_degree_factors(igp_graph* g, double tau, double eps, float* dinv, void* stream);
@@ -338,6 +353,46 @@ igp_status igp_server_get_stats(igp_server* sv, igp_server_stats* stats);
  */
 igp_status igp_embed_noalloc(const int32_t* row_ptr, const int32_t* col, int32_t N, double tau, int32_t L, int32_t d,
                              uint64_t seed, float* out, const igp_embed_opts* opts, void* stream);
+
+/*
+ * K-agnostic clustering of embeddings on the device: the step that turns the FFP output into
+ * blocks (Alg. 1's last step; Alg. 2's fit and assign), done by BIRCH in the paper (Sec. IV-A).
+ * The clusterer keeps BIRCH's leaf entries, clustering features CF = (n, LS, SS) (member count,
+ * linear sum, sum of squared norms; Zhang, Ramakrishnan, Livny, SIGMOD 1996), and its absorption
+ * rule, without the tree: the closest entry is found by an exhaustive search on the GPU. A fit
+ * takes the points in index order, in batches of `batch`:
+ *   - points are quantised to multiples of 2^-16 (they must lie in [-1, 1]; FFP outputs do);
+ *   - each point joins the entry whose centroid is closest (fp32 squared distance, coordinates
+ *     summed in order; ties to the smaller id) if the merged entry's radius
+ *     sqrt(SS/n - |LS/n|^2) (fp64 from exact integer sums) is at most `threshold`; the entries
+ *     are those at the start of the point's batch;
+ *   - the batch's other points ("candidates") form new entries: a candidate is a leader if no
+ *     earlier candidate of the batch lies within `threshold` of it; the others join the closest
+ *     leader within `threshold` (ties to the smaller index) or start an entry of their own; new
+ *     entries are numbered on in index order.
+ * The number of entries K follows from the threshold (it is not given). Labels and entries are
+ * reproducible bit for bit (integer sums, fixed-order fp32/fp64 decisions).
+ */
+typedef struct igp_clusterer igp_clusterer;
+
+/* d in {8, 16, 32, 64, 128}; threshold > 0; 1 <= batch <= 4096; 1 <= max_entries <= 2^24.
+ * The clusterer belongs to the current device. Errors: IGP_E_INVAL, IGP_E_NOMEM, IGP_E_CUDA. */
+igp_status igp_clusterer_create(int32_t d, double threshold, int32_t batch, int32_t max_entries,
+                                igp_clusterer** out);
+/* Fit N more points (a partial fit: the entries so far are kept and grown).
+ *   E      : N x d fp32 row-major, host or device, every coordinate in [-1, 1]
+ *   labels : N int32 (host or device, or NULL): the entry each point joined
+ * Synchronises `stream`. Errors: IGP_E_INVAL (a coordinate outside [-1, 1] or not finite: nothing
+ * is fitted), IGP_E_NOMEM (more than max_entries entries: the batches before the one that would
+ * exceed it are fitted), IGP_E_CUDA. */
+igp_status igp_clusterer_fit(igp_clusterer* c, const float* E, int32_t N, int32_t* labels, void* stream);
+/* The closest entry (fp32 squared distance to the centroids, ties to the smaller id) of each of N
+ * points, labels[N] host or device; entries unchanged. IGP_E_INVAL before any fit. */
+igp_status igp_clusterer_predict(igp_clusterer* c, const float* E, int32_t N, int32_t* labels, void* stream);
+/* K (number of entries) and, if non-NULL, the K x d centroids and K member counts (host or device). */
+igp_status igp_clusterer_info(igp_clusterer* c, int32_t* K, float* centroids, int64_t* counts, void* stream);
+/* Release the clusterer (waits for the legacy default stream). NULL is a no-op. */
+void igp_clusterer_free(igp_clusterer* c);
 
 /* Per-phase device timing. Events are recorded on the call's stream around each phase. */
 igp_status igp_profile_create(igp_profile** p);

@@ -109,6 +109,8 @@ _SIGS = {
     "igp_graph_info": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
     "igp_graph_export": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "igp_graph_import": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                          ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "igp_degree_factors": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
                                             ctypes.c_void_p]),
     "igp_graph_free": (None, [ctypes.c_void_p]),
@@ -120,6 +122,15 @@ _SIGS = {
     "igp_embed_noalloc": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double,
                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p,
                                            ctypes.POINTER(EmbedOpts), ctypes.c_void_p]),
+    "igp_clusterer_create": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_void_p)]),
+    "igp_clusterer_fit": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
+    "igp_clusterer_predict": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.c_void_p]),
+    "igp_clusterer_info": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p]),
+    "igp_clusterer_free": (None, [ctypes.c_void_p]),
     "igp_batch_create": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_void_p)]),
     "igp_batch_info": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
@@ -325,6 +336,15 @@ def graph_build(src, dst, N, stream=None, profile=None):
     return Graph(h.value)
 
 
+def graph_import(row_ptr, col, N, validate=True, stream=None):
+    """igp_graph_import: a Graph from a CSR (numpy arrays or tensors, host or device)."""
+    nnz = int(col.shape[0]) if col is not None else 0
+    h = ctypes.c_void_p()
+    _check(lib().igp_graph_import(_ptr(row_ptr), _ptr(col) if nnz else None, int(N), nnz, 1 if validate else 0,
+                                  _stream(stream), ctypes.byref(h)))
+    return Graph(h.value)
+
+
 def degree_factors(g, tau, eps=1e-3, out=None, stream=None):
     """igp_degree_factors: fp32 D_tau^{-1/2} (numpy array unless `out` is given)."""
     if out is None:
@@ -405,6 +425,63 @@ class Batch:
     def free(self):
         if self.handle:
             lib().igp_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Clusterer:
+    """Owning wrapper of an igp_clusterer (K-agnostic clustering on the device, BIRCH's leaf level).
+    partial_fit / predict follow the interface stream.StreamingPartitioner expects."""
+
+    def __init__(self, d, threshold, batch=1024, max_entries=1 << 20):
+        h = ctypes.c_void_p()
+        _check(lib().igp_clusterer_create(int(d), float(threshold), int(batch), int(max_entries), ctypes.byref(h)))
+        self.handle = h.value
+        self.d = int(d)
+
+    def _points(self, E):
+        if isinstance(E, np.ndarray):
+            E = np.ascontiguousarray(E, dtype=np.float32)
+        if E.shape[1] != self.d:
+            raise ValueError(f"points must have {self.d} columns")
+        return E
+
+    def fit(self, E, labels=None, stream=None):
+        """igp_clusterer_fit (a partial fit). Returns the labels (int32 numpy array unless a
+        device `labels` buffer is given)."""
+        E = self._points(E)
+        if labels is None:
+            labels = np.empty(E.shape[0], dtype=np.int32)
+        _check(lib().igp_clusterer_fit(self.handle, _ptr(E), int(E.shape[0]), _ptr(labels), _stream(stream)))
+        return labels
+
+    partial_fit = fit
+
+    def predict(self, E, labels=None, stream=None):
+        E = self._points(E)
+        if labels is None:
+            labels = np.empty(E.shape[0], dtype=np.int32)
+        _check(lib().igp_clusterer_predict(self.handle, _ptr(E), int(E.shape[0]), _ptr(labels), _stream(stream)))
+        return labels
+
+    def info(self, centroids=False, counts=False):
+        """K, and the K x d centroids / K counts (numpy) if asked."""
+        K = ctypes.c_int32()
+        _check(lib().igp_clusterer_info(self.handle, ctypes.byref(K), None, None, None))
+        C = np.empty((K.value, self.d), dtype=np.float32) if centroids else None
+        n = np.empty(K.value, dtype=np.int64) if counts else None
+        if K.value and (centroids or counts):
+            _check(lib().igp_clusterer_info(self.handle, None, _ptr(C), _ptr(n), None))
+        return K.value, C, n
+
+    def free(self):
+        if self.handle:
+            lib().igp_clusterer_free(self.handle)
             self.handle = None
 
     def __del__(self):

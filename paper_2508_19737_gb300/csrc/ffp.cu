@@ -430,9 +430,18 @@ struct Raw<__nv_bfloat16> {
 };
 
 // Column sums of t and t^2 are accumulated as integers, t * 2^kQBits rounded to nearest
-// (|t| <= 1), so that they are exact and independent of the order rows are summed in.
-constexpr int kQBits = 30;
-constexpr float kQScale = 1073741824.0f;  // 2^30
+// (|t| <= 1), so that they are exact and independent of the order rows are summed in. The
+// rounding is done in the fp32 adder: t 2^22 + 1.5 2^23 lies in [2^23, 2^24], where fp32 values
+// are spaced 1 apart, so one fma rounds t 2^22 to an integer (ties to even) that sits in the low
+// bits of the result; subtracting the bits of 1.5 2^23 leaves it as an int32. (A float to int64
+// conversion would run on the FP64 unit, which is slow on this GPU.)
+constexpr int kQBits = 22;
+constexpr float kQScale = 4194304.0f;     // 2^22
+constexpr float kQMagic = 12582912.0f;    // 1.5 2^23
+constexpr unsigned kQMagicBits = 0x4B400000u;
+__device__ __forceinline__ int qfix(float t) {
+  return (int)(__float_as_uint(__fmaf_rn(t, kQScale, kQMagic)) - kQMagicBits);
+}
 
 // Heavy rows: in the single-graph layer, rows of at least layer_heavy_min(G) entries (they
 // lead the degree order) are gathered by the whole warp, one row per tile, so that no warp is
@@ -643,8 +652,8 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
         const float agg = is * fmaf(-mu, cur.wi, acc[v]);
         const float y = fmaf(theta, zi, alpha * cur.di * agg);
         const float t = tanh_for<S>(y);
-        qs[v] += __float2ll_rn(t * kQScale);
-        qq[v] += __float2ll_rn(t * t * kQScale);
+        qs[v] += qfix(t);
+        qq[v] += qfix(__fmul_rn(t, t));
         o[v] = scaled ? cur.di * t : t;
       }
       store_chunk_cs(Tout + (int64_t)r * D, o);
@@ -1012,8 +1021,8 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer_tma(
         const float agg = is * fmaf(-mu, cur.wi, acc[v]);
         const float y = fmaf(theta, zi, alpha * cur.di * agg);
         const float t = tanh_for<S>(y);
-        qs[v] += __float2ll_rn(t * kQScale);
-        qq[v] += __float2ll_rn(t * t * kQScale);
+        qs[v] += qfix(t);
+        qq[v] += qfix(__fmul_rn(t, t));
         o[v] = scaled ? cur.di * t : t;
       }
       store_chunk_cs(Tout + (int64_t)r * D, o);
@@ -1356,8 +1365,8 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer_bat
         const float agg = is * fmaf(-mu, cur.wi, acc[v]);
         const float y = fmaf(theta, zi, alpha * cur.di * agg);
         const float t = tanh_for<S>(y);
-        qs[v] += __float2ll_rn(t * kQScale);
-        qq[v] += __float2ll_rn(t * t * kQScale);
+        qs[v] += qfix(t);
+        qq[v] += qfix(__fmul_rn(t, t));
         o[v] = scaled ? cur.di * t : t;
       }
       store_chunk_cs(Tout + (int64_t)r * D, o);

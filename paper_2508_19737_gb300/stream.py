@@ -6,7 +6,10 @@ model of Sec. II numbers nodes in arrival order):
 
 * merge: the increment is merged into the device-resident cumulative CSR (igp_graph_append; the
   first step builds it, which is Alg. 1 on (V_1, E_1));
-* embed: one FFP over all N_t nodes with a fresh Theta (seed + t);
+* embed: one FFP over all N_t nodes with Theta of the cumulative size from the same seed at
+  every step, so each old node keeps its row of Theta and each new node gets a fresh one (row i
+  of Theta depends on the seed and i alone); a fresh draw of every row at every step would put
+  the rows kept from earlier steps and the new rows into unrelated coordinates;
 * extract: only the new nodes' rows leave the device (igp_embed with out_row_begin = N_(t-1));
 * fit: the clusterer is partially fitted on those rows;
 * keep: they are appended to the rows kept from earlier steps (old nodes keep the rows of the step
@@ -75,7 +78,7 @@ class StreamingPartitioner:
         else:
             row0 = self.graph.N
             self.graph.append(src, dst, N_t, stream=self.stream)
-        rows = api.embed(self.graph, self.tau, self.L, self.d, self.seed + t, stream=self.stream,
+        rows = api.embed(self.graph, self.tau, self.L, self.d, self.seed, stream=self.stream,
                          storage=self.storage, out_row_begin=row0, **self.opts)
         self.timings[t] = {"ffp_s": time.perf_counter() - t0, "new_rows": rows.shape[0]}
         self._t += 1

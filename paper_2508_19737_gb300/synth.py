@@ -199,7 +199,7 @@ def batch_dcsbm_one(G, n_lo, n_hi, deg_lo, deg_hi, gamma, ratio, k, seed=0, bloc
     return dcsbm(N, B, float(degs[k]), gamma, ratio, seed=kid)
 
 
-def split_increments(graph, T=10, mode="random", seed=0):
+def split_increments(graph, T=10, mode="random", seed=0, return_order=False):
     """Cut a drawn graph into T edge increments.
 
     mode="random": edges in a uniformly random order, T equal slices; every
@@ -209,7 +209,8 @@ def split_increments(graph, T=10, mode="random", seed=0):
     V_1..V_T (the snowball model of Sec. II); increment t holds the edges whose
     later-visited endpoint lies in V_t, and node ids are relabelled to the visit
     order so that the nodes present after step t are 0..N_t-1.
-    Returns a list of (src, dst, N_t).
+    Returns a list of (src, dst, N_t); with return_order, also the node order (order[new id] =
+    id in the drawn graph; the identity for mode="random").
     """
     rng = np.random.default_rng(seed)
     src = graph.src.astype(np.int64)
@@ -218,8 +219,9 @@ def split_increments(graph, T=10, mode="random", seed=0):
     if mode == "random":
         perm = rng.permutation(src.size)
         cuts = np.linspace(0, src.size, T + 1).round().astype(np.int64)
-        return [(src[perm[a:b]].astype(np.int32), dst[perm[a:b]].astype(np.int32), N)
+        incs = [(src[perm[a:b]].astype(np.int32), dst[perm[a:b]].astype(np.int32), N)
                 for a, b in zip(cuts[:-1], cuts[1:])]
+        return (incs, np.arange(N)) if return_order else incs
     if mode != "snowball":
         raise ValueError(mode)
     # breadth-first visit order; a component not reached from the start is entered at its
@@ -255,7 +257,7 @@ def split_increments(graph, T=10, mode="random", seed=0):
     for t in range(T):
         m = step == t
         out.append((su[m].astype(np.int32), sv[m].astype(np.int32), int(bounds[t + 1])))
-    return out
+    return (out, order) if return_order else out
 
 
 # ---------------------------------------------------------------------------
@@ -318,6 +320,15 @@ SERVE_WORKLOADS = {
     "dcsbm-serve": dict(stream=dict(G=32, n_lo=5000, n_hi=1_000_000, mean_deg=25, gamma=2.5, ratio=5, T=10,
                                     rate=200.0, seed=0),
                         d=64, tau=-0.5, L=10, storage="bf16"),
+}
+
+
+# Alg. 2 on a graph shaped like the paper's benchmark graphs: 10 snowball increments of a
+# 100,000-node graph, Table II's streaming setting for N = 100K (tau = -100, L = 20, d = 32),
+# the device clusterer with threshold 1.0 in batches of 1,024.
+STREAM_WORKLOADS = {
+    "challenge-stream-100k": dict(N=100_000, T=10, seed=5, tau=-100.0, L=20, d=32, storage="f32", threshold=1.0,
+                                  batch=1024),
 }
 
 

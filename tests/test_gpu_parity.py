@@ -309,3 +309,47 @@ def test_bounded_device_wait_reports_timeout(api):
     ref = oracle.ffp(rp, col, oracle.theta_input(2, g.N, 64), -0.5, 3)
     assert row_rel_err(out.cpu().numpy(), ref) <= TOL["bf16"]
     gr.free()
+
+
+# ---------------------------------------------------------------------------- import
+def test_import_restores_an_exported_graph(api):
+    """igp_graph_export -> igp_graph_import (host and device arrays, validated or trusted) gives a
+    graph whose CSR, degree factors and embeddings equal the original's bit for bit."""
+    import torch
+    g = synth.dcsbm(20011, 16, 22, 2.4, 5, seed=31)
+    gr = api.graph_build(g.src, g.dst, g.N)
+    rp, col = gr.export()
+    ref = torch.empty((g.N, 32), dtype=torch.float32, device="cuda")
+    api.embed(gr, -0.5, 6, 32, 3, out=ref, storage="bf16")
+    for where, validate in (("host", True), ("device", True), ("device", False)):
+        a, b = (rp, col) if where == "host" else (_dev(rp), _dev(col))
+        h = api.graph_import(a, b, g.N, validate=validate)
+        assert h.info() == gr.info()
+        rp2, col2 = h.export()
+        assert np.array_equal(rp2, rp) and np.array_equal(col2, col)
+        out = torch.empty((g.N, 32), dtype=torch.float32, device="cuda")
+        api.embed(h, -0.5, 6, 32, 3, out=out, storage="bf16")
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+        h.free()
+    gr.free()
+
+
+def test_import_rejects_what_is_not_a_simple_undirected_csr(api):
+    rp, col = oracle.build_csr([0, 0, 1, 2], [1, 2, 2, 3], 5)  # path-like graph + isolated node 4
+    rp = rp.astype(np.int32)
+    col = col.astype(np.int32)
+    ok = api.graph_import(rp, col, 5)
+    assert ok.info()[:2] == (5, 8)
+    ok.free()
+    cases = {
+        "row_ptr": (np.array([1, 2, 4, 6, 8, 8], np.int32), col),
+        "column out of range": (rp, np.where(np.arange(col.size) == 3, 9, col).astype(np.int32)),
+        "row not sorted": (rp, col[[1, 0, 2, 3, 4, 5, 6, 7]]),
+        "self-loop": (rp, np.where(np.arange(col.size) == 0, 0, col).astype(np.int32)),
+        "not symmetric": (rp, np.where(np.arange(col.size) == 7, 1, col).astype(np.int32)),
+    }
+    for name, (a, b) in cases.items():
+        with pytest.raises(api.IgpError) as e:
+            api.graph_import(a, b, 5)
+        assert e.value.status == api.IGP_E_INVAL and name.split()[0] in str(e.value), (name, str(e.value))

@@ -170,7 +170,7 @@ def test_streaming_partitioner_equals_fresh_runs_step_by_step(api):
         acc_s.append(s)
         acc_d.append(d)
         fresh = api.graph_build(np.concatenate(acc_s), np.concatenate(acc_d), n)
-        Z = api.embed(fresh, -0.5, 6, 32, 9 + t, storage="bf16")
+        Z = api.embed(fresh, -0.5, 6, 32, 9, storage="bf16")
         fresh.free()
         ref.partial_fit(Z[n_prev:])
         kept.append(Z[n_prev:])

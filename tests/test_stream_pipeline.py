@@ -91,9 +91,9 @@ def test_each_step_fits_the_new_rows_and_predicts_every_node(monkeypatch):
     for t, (s, d, n) in enumerate(incs):
         acc_s.append(s)
         acc_d.append(d)
-        Z = oracle.ffp_from_edges(np.concatenate(acc_s), np.concatenate(acc_d), n, oracle.theta_input(40 + t, n, 8),
+        Z = oracle.ffp_from_edges(np.concatenate(acc_s), np.concatenate(acc_d), n, oracle.theta_input(40, n, 8),
                                   -0.5, 3).astype(np.float32)
-        assert fake.embedded[t] == (40 + t, n_prev)  # fresh Theta per step, new rows only
+        assert fake.embedded[t] == (40, n_prev)  # one seed: old nodes keep their Theta rows; new rows only
         assert np.array_equal(cl.fits[t], Z[n_prev:])  # partial fit on the new rows
         assert labs[t].shape == (n,)
         n_prev = n
@@ -150,7 +150,7 @@ def test_birch_in_the_pipeline_equals_birch_run_step_by_step(monkeypatch):
     for t, (s, d, n) in enumerate(incs):
         acc_s.append(s)
         acc_d.append(d)
-        Z = oracle.ffp_from_edges(np.concatenate(acc_s), np.concatenate(acc_d), n, oracle.theta_input(2 + t, n, 8),
+        Z = oracle.ffp_from_edges(np.concatenate(acc_s), np.concatenate(acc_d), n, oracle.theta_input(2, n, 8),
                                   -0.5, 3).astype(np.float32)
         ref_cl.partial_fit(Z[n_prev:])
         kept.append(Z[n_prev:])
