@@ -12,8 +12,9 @@ the directed CSR entries (twice the undirected edges).
 The default run (the 2M-node workload, one GPU) also measures the other configurations and adds
 them as keys of the same JSON line: c2_f32 and c2_bf16 (the 200K-node graph, each with its own
 roofline), batched (512 uneven graphs in one batch against the same graphs one at a time in
-fp32) and served (the Poisson stream of snapshot requests: p50/p99 per snapshot and per graph,
-throughput against serial fp32). --no-extras skips them.
+fp32), served (the Poisson stream of snapshot requests: p50/p99 per snapshot and per graph,
+throughput against serial fp32) and streaming_vs_static (Alg. 2 step by step against Alg. 1
+re-run at every step, with the device clusterer). --no-extras skips them.
 
 Multi-GPU (torchrun): every rank runs an independent replica of the workload
 (the FFP of one graph does not shard); value = units of all ranks / max time.
@@ -185,46 +186,37 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-class OracleSample:
-    """The FP64 oracle, as it stands, timed on a bounded sample of the workload: one Eq. 4
-    layer (oracle conv + tanh + ZNorm statistics) over a leading slice of the rows of the
-    workload graph. The oracle's CSR, Eq. 1 factors and Theta are prepared once, untimed;
-    the slice is sized once so that a pass takes about `budget_s`."""
+class COracle:
+    """The FP64 oracle's C version (oracle/ffp_ref.c, as it stands) on all host cores: whole FFPs
+    (Eq. 1 factors, L' layers, output) of the workload graph. The oracle's CSR is built once and
+    the input drawn once, untimed."""
 
-    def __init__(self, g, wl, budget_s):
+    def __init__(self, g, wl):
         import oracle
-        self.oracle = oracle
-        self.rp, col = oracle.build_csr(g.src, g.dst, g.N)
-        dinv = oracle.inv_sqrt_degrees(oracle.degree_correction(oracle.degrees(self.rp), wl["tau"]))
-        self.Ahat = oracle.normalized_adjacency(self.rp, col, dinv)
-        self.d = wl["d"]
-        self.N = g.N
-        self.X = oracle.theta_input(0, g.N, self.d)
-        rows = min(g.N, 20000)
-        while True:
-            dt = self._pass(rows)
-            if dt >= budget_s or rows == g.N:
-                break
-            rows = min(g.N, int(rows * max(1.5, 1.1 * budget_s / max(dt, 1e-3))))
-        self.rows = rows
+        from oracle import cffp
+        self.cffp = cffp
+        self.rp, self.col = oracle.build_csr(g.src, g.dst, g.N)
+        self.N, self.d, self.tau = g.N, wl["d"], wl["tau"]
+        self.nnz = int(self.rp[-1])
+        self.X = synth.gaussian_input(0, g.N, self.d)
+        self.cores = cffp.threads()
 
-    def _pass(self, rows):
+    def run(self, L):
         t0 = time.perf_counter()
-        T = np.tanh(self.oracle.conv_rows(self.Ahat, self.X, 0, rows, 1.0, 0.1))
-        self.oracle.znorm(T, 1)
-        return time.perf_counter() - t0
+        self.cffp.ffp(self.rp, self.col, self.X, self.tau, L)
+        dt = time.perf_counter() - t0
+        return float(self.nnz) * self.d * L / dt, dt
 
-    def rate(self):
-        dt = self._pass(self.rows)
-        return float(self.rp[self.rows]) * self.d / dt, dt
-
-    def describe(self, dt):
-        return (f"one Eq. 4 layer of the FP64 oracle (numpy/scipy, single thread) over rows 0..{self.rows - 1} of "
-                f"the {self.N}-node graph ({int(self.rp[self.rows])} of {int(self.rp[-1])} CSR entries, "
-                f"d={self.d}), {dt:.2f} s per pass")
+    def describe(self, L, dt):
+        return (f"the whole FFP (Eq. 1 factors, {L} Eq. 4 layers, output) of the {self.N}-node graph "
+                f"({self.nnz} CSR entries, d={self.d}) by the FP64 oracle in C on {self.cores} host threads "
+                f"(OpenMP), {dt:.2f} s per FFP; the oracle's CSR built beforehand, untimed")
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (its C version, all host cores) on the same workload.
+    A step is one FFP of L' <= L layers, L' chosen so that the whole run ends within a few
+    minutes; the rate counts the layers run."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
@@ -233,11 +225,13 @@ def run_reference(args):
         return 0
     wl = synth.WORKLOADS[args.workload]
     g = synth.workload_graph(args.workload)
-    budget = max(0.2, min(10.0, 90.0 / max(1, args.steps + args.warmup)))
-    smp = OracleSample(g, wl, budget)
+    ref = COracle(g, wl)
+    _, t1 = ref.run(1)
+    budget = max(0.5, min(30.0, 150.0 / max(1, args.steps + args.warmup)))
+    Ls = int(max(1, min(wl["L"], budget // max(t1, 1e-3))))
     rates, dts = [], []
     for k in range(args.warmup + args.steps):
-        r, dt = smp.rate()
+        r, dt = ref.run(Ls)
         if k >= args.warmup:
             rates.append(r)
             dts.append(dt)
@@ -246,9 +240,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(dts), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, **wl["graph"], "d": wl["d"], "tau": wl["tau"], "L": wl["L"]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": smp.describe(statistics.mean(dts))},
+        "config": {"workload": args.workload, **wl["graph"], "d": wl["d"], "tau": wl["tau"], "L": wl["L"],
+                   "layers_per_step": Ls},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": ref.cores, "kind": "oracle",
+                         "sample": ref.describe(Ls, statistics.mean(dts))},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -310,7 +305,10 @@ def batch_measure(api, torch, name, storage, d, steps, warmup, local):
     torch.cuda.synchronize()
     ph = prof.read()
     prof.close()
-    layer_s = ph["layer"][0] / max(ph["layer"][1], 1) / 1e3
+    # device time per layer: the layer phase of one profiled embedding over its L layers (one launch
+    # per layer, or one persistent launch for all of them, whichever plan the schedule tuner chose)
+    layer_s = ph["layer"][0] / max(L, 1) / 1e3
+    layer_launches = int(ph["layer"][1])
     lb = layer_bytes(N, nnz, d, sb)
     peak, peak_src = peaks()
     # the same graphs one at a time, fp32
@@ -338,7 +336,8 @@ def batch_measure(api, torch, name, storage, d, steps, warmup, local):
                    "l2": "inputs larger than L2" if N * d * sb > L2_BYTES else "working set may fit L2"},
         "roofline": {"bound": "hbm", "achieved": lb / layer_s / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": lb / layer_s / 1e9 / peak, "traffic": None, "kernel": "k_layer_batch",
-                     "avg_launch_ms": layer_s * 1e3, "algorithmic_bytes_per_launch": lb,
+                     "avg_layer_ms": layer_s * 1e3, "algorithmic_bytes_per_layer": lb,
+                     "layer_launches_per_embedding": layer_launches,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else
                      "fallback 6800 GB/s"},
         "sequential_fp32": {"value": seq_value, "unit": UNIT, "ms_per_pass": seq_ms,
@@ -707,6 +706,7 @@ def extras(api, torch, args, local):
     wl = synth.SERVE_WORKLOADS["dcsbm-serve"]
     out["served"] = serve_measure(api, torch, "dcsbm-serve", wl["storage"], wl["d"], args.slots, args.batch_rows,
                                   3, local)
+    out["streaming_vs_static"] = stream_measure(api, torch, "challenge-stream-100k", local)
     return out
 
 
@@ -747,9 +747,9 @@ def main():
         return 0
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        smp = OracleSample(ctx["g"], wl, 10.0)
-        rate, dt = smp.rate()
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": smp.describe(dt)}
+        ref = COracle(ctx["g"], wl)
+        rate, dt = ref.run(wl["L"])
+        cpu = {"value": rate, "unit": UNIT, "cores": ref.cores, "kind": "oracle", "sample": ref.describe(wl["L"], dt)}
     line = {
         "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",

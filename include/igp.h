@@ -228,12 +228,25 @@ igp_status igp_batch_info(const igp_batch* b, int32_t* G, int32_t* N_total, int6
  *   seeds : host array of G Theta seeds (graph g's rows draw Theta with seeds[g] and local row ids)
  *   out   : N_total x d fp32 (host or device); graph g's rows at row_offsets[g] ..
  *   opts  : as igp_embed, except x_in, chunk_cols and TMA gathers (not supported here)
- * With device output and no profile, the launch sequence is captured into a CUDA graph on first
- * use and replayed while (tau, L, d, options, out) stay the same; the replay runs on a library
- * stream ordered after, and before, the caller's `stream` by events.
+ * The layers run in one of two plans, both with the same arithmetic (the results are identical):
+ * one launch per layer plus a statistics launch, or one persistent cooperative launch for all L
+ * layers, in which each graph moves to its next layer as soon as its own rows are done (Eq. 4's
+ * statistics are per graph), with bounded device-side waits. On the first embedding at a (d,
+ * storage, mean-degree bucket) in the process, a schedule tuner times every candidate plan (claim
+ * sizes, CTAs per SM) on this batch and keeps the fastest for that key. With device output, no
+ * profile and the per-layer plan, the launch sequence is captured into a CUDA graph on first use
+ * and replayed while (tau, L, d, options, out) stay the same; the replay runs on a library stream
+ * ordered after, and before, the caller's `stream` by events. Errors: as igp_embed, and
+ * IGP_E_TIMEOUT (host output) when a bounded wait of the persistent launch ran out (device output:
+ * reported by igp_batch_sync).
  */
 igp_status igp_batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uint64_t* seeds, float* out,
                            const igp_embed_opts* opts, void* stream);
+
+/* Wait for the batch's last embedding; IGP_E_TIMEOUT if a bounded device-side wait of its persistent
+ * launch ran out (about a second without progress: its output is then invalid), else IGP_OK or
+ * IGP_E_CUDA. */
+igp_status igp_batch_sync(igp_batch* b);
 
 /* Release a batch (waits for its work). NULL is a no-op. */
 void igp_batch_free(igp_batch* b);

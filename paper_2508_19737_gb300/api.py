@@ -136,6 +136,7 @@ _SIGS = {
     "igp_batch_info": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
                                         ctypes.c_void_p]),
+    "igp_batch_sync": (ctypes.c_int32, [ctypes.c_void_p]),
     "igp_batch_embed": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(EmbedOpts),
                                          ctypes.c_void_p]),
@@ -421,6 +422,11 @@ class Batch:
         _check(lib().igp_batch_embed(self.handle, float(tau), int(L), int(d), sd.ctypes.data, _ptr(out),
                                      ctypes.byref(opts), _stream(stream)))
         return out
+
+    def sync(self):
+        """igp_batch_sync: wait for the last embedding; raises IgpError(IGP_E_TIMEOUT) if a bounded
+        device-side wait of its persistent launch ran out."""
+        _check(lib().igp_batch_sync(self.handle))
 
     def free(self):
         if self.handle:

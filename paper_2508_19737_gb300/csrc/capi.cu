@@ -490,6 +490,8 @@ static void batch_release(igp_batch* b) {
   if (b->cs) cudaStreamDestroy(b->cs);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->ev_err) cudaEventDestroy(b->ev_err);
+  if (b->err_host) cudaFreeHost(b->err_host);
   cudaGetLastError();
   delete b;
 }
@@ -553,7 +555,7 @@ igp_status igp_batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const
     return IGP_E_INVAL;
   }
   if (o.x_in || o.chunk_cols != 0 || (o.gather != IGP_GATHER_AUTO && o.gather != IGP_GATHER_LSU) ||
-      o.reserved_test || o.out_row_begin != 0) {
+      (o.reserved_test != 0 && (o.reserved_test < 2 || o.reserved_test > 5)) || o.out_row_begin != 0) {
     set_error("igp_batch_embed: x_in, chunk_cols, TMA gathers and out_row_begin are not supported for batches");
     return IGP_E_INVAL;
   }
@@ -569,7 +571,26 @@ igp_status igp_batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const
   igp_status st = batch_embed(b, tau, L, d, seeds, (float*)tmp, o, s);
   if (st == IGP_OK) st = copy_out(out, tmp, bytes, s);
   dev_free(tmp, s);
+  if (st == IGP_OK && b->err_host && *b->err_host) {
+    set_error("igp_batch_embed: a bounded device-side wait of the persistent launch ran out; the output is invalid");
+    *b->err_host = 0;
+    return IGP_E_TIMEOUT;
+  }
   return st;
+}
+
+igp_status igp_batch_sync(igp_batch* b) {
+  clear_error();
+  if (!b) return IGP_E_INVAL;
+  if (b->ev_out) IGP_TRY_CUDA(cudaEventSynchronize(b->ev_out));
+  if (b->ev_err) IGP_TRY_CUDA(cudaEventSynchronize(b->ev_err));
+  if (b->err_host && *b->err_host) {
+    set_error("igp_batch_sync: a bounded device-side wait of the last persistent launch ran out; its output is "
+              "invalid");
+    *b->err_host = 0;
+    return IGP_E_TIMEOUT;
+  }
+  return IGP_OK;
 }
 
 void igp_batch_free(igp_batch* b) { batch_release(b); }

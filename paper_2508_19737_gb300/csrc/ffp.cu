@@ -1380,6 +1380,310 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer_bat
   flush();
 }
 
+// ------------------------------------------------------------------ batches, one persistent launch
+// All L layers of a batch in one cooperative launch (every CTA resident). Warps claim chunks of a
+// queue of (layer, position) pairs, layer-major; a tile of graph g at layer l needs g's layer l-1
+// complete, which the warp that completes it announces: every warp adds its column sums and its
+// row count for (g, l) when it leaves (g, l); the one whose count completes g's rows forms g's
+// mean and 1/std, clears the sums and the count, and publishes ready[g] = l. So a graph moves to
+// its next layer as soon as its own rows are done, without a barrier over the batch. Claims are
+// in queue order and every earlier chunk is held by a resident warp, so every wait ends; each is
+// still bounded (about a second of globaltimer), after which the warp sets *err and returns.
+// Rows of T written in this launch are read through L2 only (ld.cg): L1 is not coherent with
+// other SMs' stores within one launch.
+template <typename S>
+struct RawCg;
+template <>
+struct RawCg<float> {
+  static __device__ __forceinline__ float4 load(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+};
+template <>
+struct RawCg<__nv_bfloat16> {
+  static __device__ __forceinline__ uint4 load(const __nv_bfloat16* p) {
+    return __ldcg(reinterpret_cast<const uint4*>(p));
+  }
+};
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Lane 0 waits until ready[g] >= l (acquire), at most about a second; the result goes to all lanes.
+// false: the wait ran out (err set) or another warp already gave up (err seen).
+__device__ __forceinline__ bool wait_ready(const int* ready, int g, int l, int* err) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0 && ld_acquire(ready + g) < l) {
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
+      __nanosleep(128);
+      if (ld_acquire(ready + g) >= l) break;
+      if (ld_acquire(err)) {
+        ok = 0;
+        break;
+      }
+      if (globaltimer_ns() - t0 > 1000000000ull) {
+        atomicOr(err, 1);
+        ok = 0;
+        break;
+      }
+    }
+  }
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+template <int D, typename S>
+__global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_ffp_batch_persistent(
+    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const float* __restrict__ dinv,
+    const float* __restrict__ wsum, const int32_t* __restrict__ perm, const int32_t* __restrict__ pgraph, int64_t P,
+    int L, S* __restrict__ T0, S* __restrict__ T1, float* __restrict__ stats, unsigned long long* __restrict__ gsum,
+    unsigned* __restrict__ rows_done, int* __restrict__ ready, const int32_t* __restrict__ goff,
+    unsigned long long* __restrict__ qctr, int* __restrict__ err, int32_t G, float alpha, float theta, int ddof,
+    int chunk, int withhold) {
+  using RT = typename Raw<S>::T;
+  constexpr int VPL = Store<S>::VPL;
+  constexpr int GW = D / VPL;  // lanes per row
+  constexpr int GPW = 32 / GW;
+  constexpr int C = layer_chunk(GW);
+  constexpr int IPL = C >= GW ? C / GW : 1;
+  static_assert(kBatchAlign % GPW == 0, "tiles must not straddle graphs");
+
+  __shared__ float s_mu[kLayerWarps][D], s_is[kLayerWarps][D];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane / GW, lig = lane % GW;
+  const uint64_t pol_first = evict_first_policy();
+  const int64_t Q = (int64_t)L * P;
+  auto claim = [&]() -> int64_t {
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(qctr, 1ull);
+    return (int64_t)__shfl_sync(0xffffffffu, c, 0) * chunk;
+  };
+
+  long long qs[VPL], qq[VPL];
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) qs[v] = qq[v] = 0;
+  int cur_g = -1, cur_l = 0;
+  unsigned rows = 0;  // rows of (cur_g, cur_l) this warp has finished since its last flush
+  // Add this warp's sums and row count of (cur_g, cur_l); the warp that completes the graph's rows
+  // forms its statistics for layer cur_l and publishes ready[cur_g] = cur_l.
+  auto flush = [&]() {
+#pragma unroll
+    for (int m = GW; m < 32; m <<= 1) {
+#pragma unroll
+      for (int v = 0; v < VPL; ++v) {
+        qs[v] += __shfl_xor_sync(0xffffffffu, qs[v], m);
+        qq[v] += __shfl_xor_sync(0xffffffffu, qq[v], m);
+      }
+    }
+    if (cur_g >= 0 && rows > 0) {
+      unsigned long long* gs = gsum + (int64_t)cur_g * 2 * D;
+      if (grp == 0) {
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+          atomicAdd(gs + lig * VPL + v, (unsigned long long)qs[v]);
+          atomicAdd(gs + D + lig * VPL + v, (unsigned long long)qq[v]);
+        }
+      }
+      __threadfence();
+      __syncwarp();
+      unsigned last = 0;
+      if (lane == 0) {
+        const unsigned n = (unsigned)(goff[cur_g + 1] - goff[cur_g]) + ((withhold && cur_g == 0) ? 1u : 0u);
+        last = atomicAdd(rows_done + cur_g, rows) + rows == n;
+      }
+      if (__shfl_sync(0xffffffffu, last, 0)) {
+        __threadfence();
+        const double n = (double)(goff[cur_g + 1] - goff[cur_g]);
+        float* so = stats + ((int64_t)(cur_l & 1) * G + cur_g) * 2 * D;
+        for (int c = lane; c < D; c += 32) {
+          const long long sa = (long long)__ldcg(gs + c), qa = (long long)__ldcg(gs + D + c);
+          const double st = (double)sa * (1.0 / (double)(1ll << kQBits));
+          const double sq = (double)qa * (1.0 / (double)(1ll << kQBits));
+          const double mean = st / n;
+          const double denom = n - (double)ddof;
+          double var = denom > 0.0 ? (sq - st * mean) / denom : 0.0;
+          if (!(var > 0.0)) var = 0.0;
+          const double sd = sqrt(var);
+          so[c] = (float)mean;
+          so[D + c] = sd > 0.0 ? (float)(1.0 / sd) : 0.0f;
+          gs[c] = 0ull;
+          gs[D + c] = 0ull;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          rows_done[cur_g] = 0u;
+          __threadfence();
+          st_release(ready + cur_g, cur_l);
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) qs[v] = qq[v] = 0;
+    rows = 0;
+  };
+  auto load_idx = [&](int (&jw)[IPL], int base, int end) {
+#pragma unroll
+    for (int k = 0; k < IPL; ++k) {
+      const int t = lig + GW * k;
+      jw[k] = (t < C && base + t < end) ? ld_stream(col + base + t, pol_first) : 0;
+    }
+  };
+
+  struct RowData {
+    int r, b, e;
+    RT self;
+    float di, wi;
+  };
+  const S* __restrict__ Tin = T0;
+  S* __restrict__ Tout = T1;
+  // A queue position as (layer - 1, position in the order); converted from the claimed chunk's
+  // queue index once per chunk (one 64-bit division), then advanced by adding GPW.
+  struct Pos {
+    int64_t l, p;  // l = Q marks the end of the queue
+  };
+  auto at = [&](int64_t qq) -> Pos {
+    if (qq >= Q) return Pos{(int64_t)L, 0};
+    const int64_t l = qq / P;
+    return Pos{l, qq - l * P};
+  };
+  // row data of the tile at position x (its T row read through L2)
+  auto fetch = [&](const Pos& x, RowData& rd) {
+    rd.r = __ldg(perm + x.p + grp);
+    rd.b = rd.e = 0;
+    rd.di = rd.wi = 0.0f;
+    rd.self = Raw<S>::zero();
+    if (rd.r >= 0) {
+      rd.b = __ldg(row_ptr + rd.r);
+      rd.e = __ldg(row_ptr + rd.r + 1);
+      rd.di = __ldg(dinv + rd.r);
+      rd.wi = __ldg(wsum + rd.r);
+      rd.self = RawCg<S>::load(Tin + (int64_t)rd.r * D + lig * VPL);
+    }
+  };
+  auto graph_of = [&](const Pos& x) -> int { return __ldg(pgraph + x.p / kBatchAlign); };
+  // the position after x in this warp's sequence (a chunk is claimed one chunk ahead)
+  int64_t next_chunk = claim();
+  int left = chunk / GPW;  // tiles left in the current chunk
+  auto advance = [&](const Pos& x) -> Pos {
+    if (--left > 0) {
+      Pos y{x.l, x.p + GPW};
+      if (y.p == P) {
+        y.l += 1;
+        y.p = 0;
+      }
+      return y;
+    }
+    left = chunk / GPW;
+    const int64_t c = next_chunk;
+    if (c < Q) next_chunk = claim();
+    return at(c);
+  };
+  // enter the segment (layer x.l + 1, graph g): flush the last one, wait for the graph's previous
+  // layer, load its statistics and pick the layer's buffers; false if a wait gave up
+  auto enter = [&](const Pos& x, int g) -> bool {
+    const int l = (int)x.l + 1;
+    flush();
+    cur_g = g;
+    cur_l = l;
+    if (l > 1 && !wait_ready(ready, g, l - 1, err)) return false;
+    const float* si = stats + ((int64_t)((l - 1) & 1) * G + g) * 2 * D;
+    for (int c = lane; c < D; c += 32) {
+      s_mu[warp][c] = l > 1 ? __ldcg(si + c) : 0.0f;
+      s_is[warp][c] = l > 1 ? __ldcg(si + D + c) : 1.0f;
+    }
+    __syncwarp();
+    Tin = (l & 1) ? T0 : T1;  // layer l reads T^(l-1) and writes T^(l); T0 holds Theta
+    Tout = (l & 1) ? T1 : T0;
+    return true;
+  };
+
+  Pos x = at(next_chunk);
+  if (next_chunk < Q) next_chunk = claim();
+  if (x.l >= L) {
+    flush();
+    return;
+  }
+  int gx = graph_of(x);
+  if (!enter(x, gx)) return;
+  RowData cur;
+  fetch(x, cur);
+  int jw[IPL];
+  load_idx(jw, cur.b, cur.e);
+  Pos xn = advance(x);
+  while (true) {
+    // the next tile's data is read during this tile's gathers when it belongs to the same segment
+    // (its dependency is then already met); otherwise after the switch
+    const int gn = xn.l < L ? graph_of(xn) : -1;
+    const bool same = xn.l == x.l && gn == gx;
+    RowData nxt;
+    if (same) fetch(xn, nxt);
+    const int mtrip = __reduce_max_sync(0xffffffffu, (cur.e - cur.b + C - 1) / C);
+    float acc[VPL];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) acc[v] = 0.0f;
+    for (int tr = 0; tr < mtrip; ++tr) {
+      const int c = cur.b + tr * C;
+      int jn[IPL];
+      load_idx(jn, c + C, cur.e);
+      RT x[C];
+#pragma unroll
+      for (int t = 0; t < C; ++t) {
+        const int j = __shfl_sync(0xffffffffu, jw[t / GW], t % GW, GW);
+        x[t] = (c + t < cur.e) ? RawCg<S>::load(Tin + (int64_t)j * D + lig * VPL) : Raw<S>::zero();
+      }
+#pragma unroll
+      for (int t = 0; t < C; ++t) Raw<S>::add(acc, x[t]);
+#pragma unroll
+      for (int k = 0; k < IPL; ++k) jw[k] = jn[k];
+    }
+    if (same) load_idx(jw, nxt.b, nxt.e);
+    const int r = cur.r;
+    if (r >= 0) {
+      float sv[VPL];
+      Raw<S>::unpack(cur.self, sv);
+      const bool scaled = cur.di > 0.0f;
+      const float rdi = scaled ? __frcp_rn(cur.di) : 1.0f;
+      float o[VPL];
+#pragma unroll
+      for (int v = 0; v < VPL; ++v) {
+        const int cidx = lig * VPL + v;
+        const float mu = s_mu[warp][cidx], is = s_is[warp][cidx];
+        const float ti = scaled ? sv[v] * rdi : sv[v];
+        const float zi = (ti - mu) * is;
+        const float agg = is * fmaf(-mu, cur.wi, acc[v]);
+        const float y = fmaf(theta, zi, alpha * cur.di * agg);
+        const float t = tanh_for<S>(y);
+        qs[v] += qfix(t);
+        qq[v] += qfix(__fmul_rn(t, t));
+        o[v] = scaled ? cur.di * t : t;
+      }
+      store_chunk_cs(Tout + (int64_t)r * D + lig * VPL, o);
+    }
+    rows += __popc(__ballot_sync(0xffffffffu, lig == 0 && r >= 0));
+    x = xn;
+    gx = gn;
+    if (x.l >= L) break;
+    xn = advance(x);
+    if (same) {
+      cur = nxt;
+    } else {
+      if (!enter(x, gx)) return;
+      fetch(x, cur);
+      load_idx(jw, cur.b, cur.e);
+    }
+  }
+  flush();
+}
+
 // Per graph and column: mean and 1/std from the exact sums (then cleared for the next layer).
 template <int D>
 __global__ void k_batch_stats(unsigned long long* __restrict__ gsum, const int32_t* __restrict__ goff, int32_t G,
@@ -1629,6 +1933,64 @@ igp_status batch_layer_launch(const igp_batch* b, const void* Tin, void* Tout, c
   return after_launch("k_layer_batch");
 }
 
+// All layers of a batch in one cooperative launch (every CTA resident: the launch fails rather
+// than run part of the grid). Arguments as in k_ffp_batch_persistent.
+struct PersistArgs {
+  void *T0, *T1;
+  float* stats;
+  unsigned long long* gsum;
+  unsigned* rows_done;
+  int* ready;
+  unsigned long long* qctr;
+  int* err;
+  int L, ddof, chunk, grid, withhold;
+  float alpha, theta;
+};
+
+template <int D, typename S>
+int persist_per_sm() {
+  static int n = -1;
+  if (n < 0) {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_ffp_batch_persistent<D, S>, kLayerThreads, 0);
+    n = std::max(b, 1);
+  }
+  return n;
+}
+
+template <int D, typename S>
+igp_status batch_persist_launch(const igp_batch* b, const PersistArgs& a, cudaStream_t s) {
+  const int32_t* row_ptr = b->row_ptr;
+  const int32_t* col = b->col;
+  const float* dinv = b->dinv;
+  const float* wsum = b->wsum;
+  const int32_t* perm = b->perm;
+  const int32_t* pgraph = b->pgraph;
+  int64_t P = b->P;
+  int L = a.L;
+  S* T0 = (S*)a.T0;
+  S* T1 = (S*)a.T1;
+  float* stats = a.stats;
+  unsigned long long* gsum = a.gsum;
+  unsigned* rows_done = a.rows_done;
+  int* ready = a.ready;
+  const int32_t* goff = b->goff;
+  unsigned long long* qctr = a.qctr;
+  int* err = a.err;
+  int32_t G = b->G;
+  float alpha = a.alpha, theta = a.theta;
+  int ddof = a.ddof, chunk = a.chunk, withhold = a.withhold;
+  void* args[] = {&row_ptr, &col, &dinv, &wsum, &perm, &pgraph, &P, &L, &T0, &T1, &stats, &gsum, &rows_done,
+                  &ready, &goff, &qctr, &err, &G, &alpha, &theta, &ddof, &chunk, &withhold};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_ffp_batch_persistent<D, S>, dim3(a.grid),
+                                              dim3(kLayerThreads), args, 0, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e, "cudaLaunchCooperativeKernel(k_ffp_batch_persistent)", __FILE__, __LINE__);
+  }
+  return after_launch("k_ffp_batch_persistent");
+}
+
 template <int D, typename S>
 igp_status batch_tail_launch(const igp_batch* b, unsigned long long* gsum, int ddof, float* st_out, cudaStream_t s) {
   const int64_t n = (int64_t)b->G * D;
@@ -1660,6 +2022,8 @@ igp_status batch_theta_launch(const igp_batch* b, int d, float xs, void* out, cu
 
 struct BatchOps {
   int (*per_sm)();
+  int (*persist_per_sm)();
+  igp_status (*persist)(const igp_batch*, const PersistArgs&, cudaStream_t);
   igp_status (*layer)(const igp_batch*, const void*, void*, const float*, unsigned long long*, float, float, int,
                       int, cudaStream_t);
   igp_status (*tail)(const igp_batch*, unsigned long long*, int, float*, cudaStream_t);
@@ -1669,8 +2033,9 @@ struct BatchOps {
 
 template <int D, typename S>
 BatchOps batch_ops_for() {
-  return BatchOps{&BatchCfg<D, S>::per_sm, &batch_layer_launch<D, S>, &batch_tail_launch<D, S>,
-                  &batch_output_launch<D, S>, &batch_theta_launch<S>};
+  return BatchOps{&BatchCfg<D, S>::per_sm, &persist_per_sm<D, S>, &batch_persist_launch<D, S>,
+                  &batch_layer_launch<D, S>, &batch_tail_launch<D, S>, &batch_output_launch<D, S>,
+                  &batch_theta_launch<S>};
 }
 
 bool get_batch_ops(int d, int storage, BatchOps* o) {
@@ -2045,12 +2410,14 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
     const int64_t want = (b->P + (int64_t)kLayerWarps * chunk - 1) / ((int64_t)kLayerWarps * chunk);
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)bo.per_sm() * num_sms()));
   };
-  // workspace: T0 | T1 | stats[2][G][2d] | gsum[G][2d]
+  // workspace: T0 | T1 | stats[2][G][2d] | gsum[G][2d] + claim counter | rows_done[G] ready[G] qctr err
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t bT = al((size_t)N * d * sb);
   const size_t bS = al((size_t)2 * G * 2 * d * sizeof(float));
   const size_t bQ = al((size_t)G * 2 * d * sizeof(unsigned long long) + sizeof(unsigned long long));  // + counter
-  const size_t need = 2 * bT + bS + bQ;
+  const size_t offQ = ((size_t)G * 8 + 7) & ~(size_t)7;
+  const size_t bX = al(offQ + 16);
+  const size_t need = 2 * bT + bS + bQ + bX;
   if (b->ws_bytes < need) {
     if (b->ws) dev_free(b->ws, s);
     b->ws = nullptr;
@@ -2061,75 +2428,145 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
     b->ws_bytes = need;
     b->exec_key.clear();
   }
+  if (!b->err_host) {
+    count_alloc();
+    IGP_TRY_CUDA(cudaHostAlloc((void**)&b->err_host, sizeof(int), cudaHostAllocDefault));
+    *b->err_host = 0;
+  }
   char* base = (char*)b->ws;
   void* T0 = base;
   void* T1 = base + bT;
   float* stats = (float*)(base + 2 * bT);
   unsigned long long* gsum = (unsigned long long*)(base + 2 * bT + bS);
+  char* xb = base + 2 * bT + bS + bQ;
+  unsigned* rows_done = (unsigned*)xb;
+  int* ready = (int*)(xb + (size_t)G * 4);
+  unsigned long long* qctr = (unsigned long long*)(xb + offQ);
+  int* err = (int*)(xb + offQ + 8);
   const double xs = o.x_scale > 0 ? o.x_scale : 1.0 / std::sqrt((double)d);
+  // test hooks (reserved_test, the library's own tests only): 2 = the persistent plan with one row
+  // of graph 0 withheld, so that its bounded waits run out; 3, 4 = the persistent plan (claims of
+  // 64 at one CTA per SM; of 256 at the resident maximum); 5 = one launch per layer (claims of 64)
+  const int withhold = o.reserved_test == 2 ? 1 : 0;
 
   IGP_TRY_CUDA(cudaMemcpyAsync(b->seeds_dev, seeds, (size_t)G * 8, cudaMemcpyHostToDevice, s));
-  // Schedule tuning: on the first embedding at this (d, storage), one layer is timed for each
-  // claim size (each followed by the statistics kernel, which clears what the layer added);
-  // the fastest is kept for the batch.
-  const int tkey = d * 2 + o.storage;
-  if (!b->tuned_chunk.count(tkey)) {
-    const int nc = (int)(sizeof(kBatchChunks) / sizeof(kBatchChunks[0]));
-    cudaEvent_t ev[2 * 4];
-    for (int k = 0; k < 2 * nc; ++k) IGP_TRY_CUDA(cudaEventCreate(&ev[k]));
-    igp_status st = IGP_OK;
-    if (cudaMemsetAsync(gsum, 0, bQ, s) != cudaSuccess) st = cuda_status(cudaGetLastError(), "memset", __FILE__, __LINE__);
-    if (st == IGP_OK) st = bo.theta(b, d, (float)xs, T0, s);
-    for (int k = 0; k < nc && st == IGP_OK; ++k) {
-      cudaEventRecord(ev[2 * k], s);
-      st = bo.layer(b, T0, T1, nullptr, gsum, (float)o.alpha, (float)o.theta, grid_for(kBatchChunks[k]),
-                    kBatchChunks[k], s);
-      cudaEventRecord(ev[2 * k + 1], s);
-      if (st == IGP_OK) st = bo.tail(b, gsum, o.znorm_ddof, stats, s);
-    }
-    int best = kBatchChunks[1];
-    float best_ms = 1e30f;
-    for (int k = 0; k < nc && st == IGP_OK; ++k) {
-      float ms = 0.0f;
-      if (cudaEventSynchronize(ev[2 * k + 1]) != cudaSuccess || cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]) != cudaSuccess) {
-        st = cuda_status(cudaGetLastError(), "schedule tuning", __FILE__, __LINE__);
-        break;
-      }
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = kBatchChunks[k];
-      }
-    }
-    for (int k = 0; k < 2 * nc; ++k) cudaEventDestroy(ev[k]);
-    IGP_TRY(st);
-    b->tuned_chunk[tkey] = best;
-    b->exec_key.clear();
-  }
-  const int chunk = b->tuned_chunk[tkey];
-  const int grid = grid_for(chunk);
 
-  auto enqueue = [&](cudaStream_t q, Profile* pf) -> igp_status {
-    IGP_TRY_CUDA(cudaMemsetAsync(gsum, 0, bQ, q));
+  // One FFP of every graph with plan pl: Theta, the layers (one launch each plus a statistics
+  // launch, or one persistent launch for all of them) and the output.
+  auto enqueue_plan = [&](cudaStream_t q, Profile* pf, const igp_batch::Plan& pl) -> igp_status {
+    IGP_TRY_CUDA(cudaMemsetAsync(gsum, 0, bQ + bX, q));
     {
       PhaseTimer pt(pf, IGP_PHASE_THETA, q);
       IGP_TRY(bo.theta(b, d, (float)xs, T0, q));
     }
     const void* cur = T0;
     const float* st_prev = nullptr;
-    for (int32_t l = 1; l <= L; ++l) {
-      void* dst = (cur == T0) ? T1 : T0;
-      float* st = stats + (size_t)(l & 1) * G * 2 * d;
-      PhaseTimer pt(pf, IGP_PHASE_LAYER, q);
-      IGP_TRY(bo.layer(b, cur, dst, st_prev, gsum, (float)o.alpha, (float)o.theta, grid, chunk, q));
-      IGP_TRY(bo.tail(b, gsum, o.znorm_ddof, st, q));
-      cur = dst;
-      st_prev = st;
+    if (pl.mode == 1 && L > 0) {
+      PersistArgs a{T0, T1, stats, gsum, rows_done, ready, qctr, err, L, o.znorm_ddof, pl.chunk,
+                    pl.ctas * num_sms(), withhold, (float)o.alpha, (float)o.theta};
+      {
+        PhaseTimer pt(pf, IGP_PHASE_LAYER, q);
+        IGP_TRY(bo.persist(b, a, q));
+      }
+      IGP_TRY_CUDA(cudaMemcpyAsync(b->err_host, err, sizeof(int), cudaMemcpyDeviceToHost, q));
+      if (!b->ev_err) IGP_TRY_CUDA(cudaEventCreateWithFlags(&b->ev_err, cudaEventDisableTiming));
+      IGP_TRY_CUDA(cudaEventRecord(b->ev_err, q));
+      cur = (L & 1) ? T1 : T0;
+      st_prev = stats + (size_t)(L & 1) * G * 2 * d;
+    } else {
+      for (int32_t l = 1; l <= L; ++l) {
+        void* dst = (cur == T0) ? T1 : T0;
+        float* st = stats + (size_t)(l & 1) * G * 2 * d;
+        PhaseTimer pt(pf, IGP_PHASE_LAYER, q);
+        IGP_TRY(bo.layer(b, cur, dst, st_prev, gsum, (float)o.alpha, (float)o.theta, grid_for(pl.chunk), pl.chunk,
+                         q));
+        IGP_TRY(bo.tail(b, gsum, o.znorm_ddof, st, q));
+        cur = dst;
+        st_prev = st;
+      }
     }
     PhaseTimer pt(pf, IGP_PHASE_OUTPUT, q);
     return bo.output(b, cur, st_prev, o.out_row_l2, out_dev, q);
   };
 
-  if (prof || !capture) return enqueue(s, prof);  // timed phases, or a one-off batch: plain launches
+  // Schedule tuner: on the first embedding at a (d, storage, mean-degree bucket) in this process,
+  // every candidate plan runs one whole FFP of this batch, timed with CUDA events, and the
+  // fastest is kept for the key (later batches with the same key reuse it). Candidates: one
+  // launch per layer with each claim size, and the persistent launch with claim sizes 64 and 256
+  // at one CTA per SM and at the resident maximum.
+  const int tkey = d * 2 + o.storage;
+  igp_batch::Plan plan;
+  if (o.reserved_test >= 2 && o.reserved_test <= 5) {
+    const int t = o.reserved_test;
+    plan.mode = t == 5 ? 0 : 1;
+    plan.chunk = t == 4 ? 256 : 64;
+    plan.ctas = t == 4 ? bo.persist_per_sm() : 1;
+  } else {
+    if (!b->plan.count(tkey)) {
+      const int dbucket = (int)std::lround(std::log2(std::max(1.0, (double)b->nnz / std::max(1, N))));
+      const auto gkey = std::make_tuple(d, o.storage, dbucket);
+      static std::mutex tmu;
+      static std::map<std::tuple<int, int, int>, igp_batch::Plan> tuned;
+      bool found = false;
+      {
+        std::lock_guard<std::mutex> lk(tmu);
+        auto it = tuned.find(gkey);
+        if (it != tuned.end()) {
+          b->plan[tkey] = it->second;
+          found = true;
+        }
+      }
+      if (!found) {
+        std::vector<igp_batch::Plan> cands;
+        for (int c : kBatchChunks) cands.push_back(igp_batch::Plan{0, c, 1});
+        const int pm = bo.persist_per_sm();
+        for (int c : {64, 256}) {
+          cands.push_back(igp_batch::Plan{1, c, 1});
+          if (pm > 1) cands.push_back(igp_batch::Plan{1, c, pm});
+        }
+        std::vector<cudaEvent_t> ev(2 * cands.size() + 2, nullptr);
+        for (auto& e : ev) IGP_TRY_CUDA(cudaEventCreate(&e));
+        igp_status st = enqueue_plan(s, nullptr, cands[0]);  // warm-up (module loads, first touches)
+        for (size_t k = 0; k < cands.size() && st == IGP_OK; ++k) {
+          cudaEventRecord(ev[2 * k], s);
+          st = enqueue_plan(s, nullptr, cands[k]);
+          cudaEventRecord(ev[2 * k + 1], s);
+        }
+        igp_batch::Plan best = cands[0];
+        float best_ms = 1e30f;
+        for (size_t k = 0; k < cands.size() && st == IGP_OK; ++k) {
+          float ms = 0.0f;
+          if (cudaEventSynchronize(ev[2 * k + 1]) != cudaSuccess ||
+              cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]) != cudaSuccess) {
+            st = cuda_status(cudaGetLastError(), "schedule tuning", __FILE__, __LINE__);
+            break;
+          }
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = cands[k];
+          }
+        }
+        for (auto& e : ev) cudaEventDestroy(e);
+        if (st == IGP_OK && *b->err_host) {
+          *b->err_host = 0;
+          set_error("igp_batch_embed: a bounded device-side wait ran out while tuning the schedule");
+          st = IGP_E_TIMEOUT;
+        }
+        IGP_TRY(st);
+        b->plan[tkey] = best;
+        std::lock_guard<std::mutex> lk(tmu);
+        tuned[gkey] = best;
+      }
+      b->exec_key.clear();
+    }
+    plan = b->plan[tkey];
+  }
+  const int chunk = plan.chunk;
+
+  auto enqueue = [&](cudaStream_t q, Profile* pf) -> igp_status { return enqueue_plan(q, pf, plan); };
+
+  // timed phases, a one-off batch or the persistent launch: plain launches
+  if (prof || !capture || plan.mode == 1) return enqueue(s, prof);
   // The launch sequence is captured once into a CUDA graph (on a library stream ordered
   // after `s`) and replayed while its parameters stay the same.
   char key[256];

@@ -124,8 +124,16 @@ struct igp_batch {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t exec_kernels = 0;  // kernels in exec
-  std::map<int, int> tuned_chunk;  // claim size of the batch layer per (d, storage), timed on first use
+  // launch plan per (d, storage), chosen by the schedule tuner on first use: mode 0 = one launch
+  // per layer plus a statistics launch, 1 = one persistent launch for all layers; the claim size
+  // (order positions per warp turn); CTAs per SM of the persistent launch
+  struct Plan {
+    int mode = 0, chunk = 64, ctas = 1;
+  };
+  std::map<int, Plan> plan;
   std::string exec_key;
+  int* err_host = nullptr;        // pinned copy of the device error word of the last persistent launch
+  cudaEvent_t ev_err = nullptr;   // recorded after that copy
 };
 
 namespace igp {
