@@ -1570,22 +1570,14 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_ffp_batch
     }
   };
   auto graph_of = [&](const Pos& x) -> int { return __ldg(pgraph + x.p / kBatchAlign); };
-  // the position after x in this warp's sequence (a chunk is claimed one chunk ahead)
-  int64_t next_chunk = claim();
-  int left = chunk / GPW;  // tiles left in the current chunk
-  auto advance = [&](const Pos& x) -> Pos {
-    if (--left > 0) {
-      Pos y{x.l, x.p + GPW};
-      if (y.p == P) {
-        y.l += 1;
-        y.p = 0;
-      }
-      return y;
+  // the next position of the same chunk
+  auto step = [&](const Pos& x) -> Pos {
+    Pos y{x.l, x.p + GPW};
+    if (y.p == P) {
+      y.l += 1;
+      y.p = 0;
     }
-    left = chunk / GPW;
-    const int64_t c = next_chunk;
-    if (c < Q) next_chunk = claim();
-    return at(c);
+    return y;
   };
   // enter the segment (layer x.l + 1, graph g): flush the last one, wait for the graph's previous
   // layer, load its statistics and pick the layer's buffers; false if a wait gave up
@@ -1606,8 +1598,10 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_ffp_batch
     return true;
   };
 
-  Pos x = at(next_chunk);
-  if (next_chunk < Q) next_chunk = claim();
+  // Chunks are claimed when a warp is ready to start them (a chunk claimed ahead would hold back the
+  // completion of its graphs while the warp finishes its current chunk).
+  Pos x = at(claim());
+  int left = chunk / GPW;  // tiles of the current chunk, this one included
   if (x.l >= L) {
     flush();
     return;
@@ -1618,12 +1612,17 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_ffp_batch
   fetch(x, cur);
   int jw[IPL];
   load_idx(jw, cur.b, cur.e);
-  Pos xn = advance(x);
   while (true) {
-    // the next tile's data is read during this tile's gathers when it belongs to the same segment
-    // (its dependency is then already met); otherwise after the switch
-    const int gn = xn.l < L ? graph_of(xn) : -1;
-    const bool same = xn.l == x.l && gn == gx;
+    // the next tile of the chunk is read during this tile's gathers when it belongs to the same
+    // segment (its dependency is then already met); otherwise after the switch
+    const bool in_chunk = left > 1;
+    Pos xn = x;
+    int gn = -1;
+    if (in_chunk) {
+      xn = step(x);
+      gn = xn.l < L ? graph_of(xn) : -1;
+    }
+    const bool same = in_chunk && xn.l == x.l && gn == gx;
     RowData nxt;
     if (same) fetch(xn, nxt);
     const int mtrip = __reduce_max_sync(0xffffffffu, (cur.e - cur.b + C - 1) / C);
@@ -1669,10 +1668,16 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_ffp_batch
       store_chunk_cs(Tout + (int64_t)r * D + lig * VPL, o);
     }
     rows += __popc(__ballot_sync(0xffffffffu, lig == 0 && r >= 0));
-    x = xn;
-    gx = gn;
+    if (in_chunk) {
+      --left;
+      x = xn;
+      gx = gn;
+    } else {
+      left = chunk / GPW;
+      x = at(claim());
+      gx = x.l < L ? graph_of(x) : -1;
+    }
     if (x.l >= L) break;
-    xn = advance(x);
     if (same) {
       cur = nxt;
     } else {
