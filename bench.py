@@ -13,8 +13,9 @@ The default run (the 2M-node workload, one GPU) also measures the other configur
 them as keys of the same JSON line: c2_f32 and c2_bf16 (the 200K-node graph, each with its own
 roofline), batched (512 uneven graphs in one batch against the same graphs one at a time in
 fp32), served (the Poisson stream of snapshot requests: p50/p99 per snapshot and per graph,
-throughput against serial fp32) and streaming_vs_static (Alg. 2 step by step against Alg. 1
-re-run at every step, with the device clusterer). --no-extras skips them.
+throughput against serial fp32), streaming_vs_static (Alg. 2 step by step against Alg. 1
+re-run at every step, with the device clusterer) and clustered (the device clusterer on the FFP
+output of a 1M-node benchmark-shaped graph). --no-extras skips them.
 
 Multi-GPU (torchrun): every rank runs an independent replica of the workload
 (the FFP of one graph does not shard); value = units of all ranks / max time.
@@ -51,7 +52,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="dcsbm-2m", choices=sorted(synth.WORKLOADS) + sorted(synth.BATCH_WORKLOADS)
-                   + sorted(synth.SERVE_WORKLOADS) + sorted(synth.STREAM_WORKLOADS))
+                   + sorted(synth.SERVE_WORKLOADS) + sorted(synth.STREAM_WORKLOADS)
+                   + sorted(synth.CLUSTER_WORKLOADS))
     p.add_argument("--slots", type=int, default=8, help="concurrent requests of the served stream")
     p.add_argument("--batch-rows", type=int, default=0,
                    help="served graphs with fewer nodes share batched FFPs (0: every slot embeds its own)")
@@ -585,6 +587,64 @@ def run_stream(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- clustering
+def cluster_measure(api, torch, name, local, reps=5):
+    """The device clusterer (BIRCH's leaf level) on the FFP output of a benchmark-shaped graph: the
+    embedding stays on the device, each fit starts from an empty clusterer; reported: the fit's
+    time (CUDA events), the number of entries and the partition's NMI / pairwise F1 against the
+    planted blocks. Returns the JSON dict."""
+    from paper_2508_19737_gb300 import metrics
+    wl = synth.CLUSTER_WORKLOADS[name]
+    g = synth.challenge_like(wl["N"], seed=wl["seed"])
+    gr = api.graph_build(g.src, g.dst, g.N)
+    E = torch.empty((g.N, wl["d"]), dtype=torch.float32, device="cuda")
+    api.embed(gr, wl["tau"], wl["L"], wl["d"], 0, out=E, storage=wl["storage"])
+    gr.free()
+    lab = torch.empty(g.N, dtype=torch.int32, device="cuda")
+    warm = api.Clusterer(wl["d"], wl["threshold"], batch=wl["batch"])
+    warm.fit(E[:wl["batch"]], labels=lab[:wl["batch"]])
+    warm.free()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = []
+    n0 = api.launch_count()
+    for _ in range(reps):
+        cl = api.Clusterer(wl["d"], wl["threshold"], batch=wl["batch"])
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        cl.fit(E, labels=lab)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        K = cl.info()[0]
+        cl.free()
+    launches = (api.launch_count() - n0) // reps
+    clk = clocks.stop()
+    l = lab.cpu().numpy()
+    p, r, f1 = metrics.pairwise_scores(g.blocks, l)
+    ms = statistics.median(times)
+    return {"metric": "clustered points/s", "value": g.N / (ms / 1e3), "unit": "points/s", "ms_per_fit": ms,
+            "config": {"workload": name, **wl, "blocks": int(g.blocks.max()) + 1},
+            "entries": int(K), "nmi": metrics.nmi(g.blocks, l), "f1": f1, "precision": p, "recall": r,
+            "gpu_launches_per_fit": int(launches), "clocks": clk,
+            "what": "igp_clusterer_fit of every row of the FFP output (device memory), fresh clusterer"}
+
+
+def run_cluster(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2508_19737_gb300 import api
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    print(json.dumps(cluster_measure(api, torch, args.workload, local)), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def single_measure(api, torch, name, storage, steps, warmup, local, world=1, chunk_cols=0, gather="auto",
                    g=None, barrier=lambda: None):
@@ -707,6 +767,7 @@ def extras(api, torch, args, local):
     out["served"] = serve_measure(api, torch, "dcsbm-serve", wl["storage"], wl["d"], args.slots, args.batch_rows,
                                   3, local)
     out["streaming_vs_static"] = stream_measure(api, torch, "challenge-stream-100k", local)
+    out["clustered"] = cluster_measure(api, torch, "challenge-cluster-1m", local)
     return out
 
 
@@ -716,6 +777,8 @@ def main():
         return run_reference(args)
     if args.workload in synth.STREAM_WORKLOADS:
         return 0 if dist_env()[0] != 0 else run_stream(args)
+    if args.workload in synth.CLUSTER_WORKLOADS:
+        return 0 if dist_env()[0] != 0 else run_cluster(args)
     if args.workload in synth.BATCH_WORKLOADS or args.workload in synth.SERVE_WORKLOADS:
         if dist_env()[0] != 0:  # one process runs these modes; other ranks have nothing to do
             return 0

@@ -618,27 +618,65 @@ igp_status igp_clusterer_fit(igp_clusterer* c, const float* E, int32_t N, int32_
   const double tq = st.threshold * 65536.0;
   const double t2r = tq * tq;
   const float t2d = (float)(st.threshold * st.threshold);
-  for (int64_t b0 = 0; b0 < N; b0 += st.batch) {
-    const int m = (int)std::min<int64_t>(st.batch, N - b0);
-    if (cudaMemsetAsync(st.best, 0xff, (size_t)m * 8, s) != cudaSuccess)
-      return done(cuda_status(cudaGetLastError(), "cudaMemsetAsync", __FILE__, __LINE__));
-    ops.best(Ed, b0, m, st.C, st.ctr, st.best, dim3((m + kCluThreads - 1) / kCluThreads, slices_for(m)), s);
-    if ((e = after_launch("k_clu_best")) != IGP_OK) return done(e);
-    ops.join(Ed, b0, m, st.n, st.LS, st.SS, st.best, t2r, st.lab, st.ctr, s);
-    if ((e = after_launch("k_clu_join")) != IGP_OK) return done(e);
-    k_clu_compact<<<1, 1024, 0, s>>>(st.lab, m, st.cand, st.ctr);
-    if ((e = after_launch("k_clu_compact")) != IGP_OK) return done(e);
-    ops.leaders(Ed, b0, m, st.cand, st.ctr, t2d, st.flag, s);
-    if ((e = after_launch("k_clu_leaders")) != IGP_OK) return done(e);
-    ops.targets(Ed, b0, m, st.cand, st.ctr, st.flag, t2d, st.target, s);
-    if ((e = after_launch("k_clu_targets")) != IGP_OK) return done(e);
-    k_clu_number<<<1, 1024, 0, s>>>(st.cand, st.flag, st.target, st.cap, st.eid, st.lab, st.ctr);
-    if ((e = after_launch("k_clu_number")) != IGP_OK) return done(e);
-    ops.sums(Ed, b0, m, st.lab, st.ctr, st.n, st.LS, st.SS, lab_out, s);
-    if ((e = after_launch("k_clu_sums")) != IGP_OK) return done(e);
-    ops.centroids(m, st.lab, st.ctr, st.n, st.LS, st.C, s);
-    if ((e = after_launch("k_clu_centroids")) != IGP_OK) return done(e);
+  // The batches, in stream order: 8 launches each (and a memset), all of them reading the entry
+  // count and the error word from device memory, so the whole sequence is fixed by N and can be
+  // recorded once into a CUDA graph and launched as one; launched one by one if recording fails.
+  auto enqueue = [&](cudaStream_t q) -> igp_status {
+    for (int64_t b0 = 0; b0 < N; b0 += st.batch) {
+      const int m = (int)std::min<int64_t>(st.batch, N - b0);
+      IGP_TRY_CUDA(cudaMemsetAsync(st.best, 0xff, (size_t)m * 8, q));
+      ops.best(Ed, b0, m, st.C, st.ctr, st.best, dim3((m + kCluThreads - 1) / kCluThreads, slices_for(m)), q);
+      IGP_TRY(after_launch("k_clu_best"));
+      ops.join(Ed, b0, m, st.n, st.LS, st.SS, st.best, t2r, st.lab, st.ctr, q);
+      IGP_TRY(after_launch("k_clu_join"));
+      k_clu_compact<<<1, 1024, 0, q>>>(st.lab, m, st.cand, st.ctr);
+      IGP_TRY(after_launch("k_clu_compact"));
+      ops.leaders(Ed, b0, m, st.cand, st.ctr, t2d, st.flag, q);
+      IGP_TRY(after_launch("k_clu_leaders"));
+      ops.targets(Ed, b0, m, st.cand, st.ctr, st.flag, t2d, st.target, q);
+      IGP_TRY(after_launch("k_clu_targets"));
+      k_clu_number<<<1, 1024, 0, q>>>(st.cand, st.flag, st.target, st.cap, st.eid, st.lab, st.ctr);
+      IGP_TRY(after_launch("k_clu_number"));
+      ops.sums(Ed, b0, m, st.lab, st.ctr, st.n, st.LS, st.SS, lab_out, q);
+      IGP_TRY(after_launch("k_clu_sums"));
+      ops.centroids(m, st.lab, st.ctr, st.n, st.LS, st.C, q);
+      IGP_TRY(after_launch("k_clu_centroids"));
+    }
+    return IGP_OK;
+  };
+  bool ran = false;
+  if (N > st.batch) {  // several batches: record them (on a private stream ordered after s)
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventRecord(ev, s) == cudaSuccess && cudaStreamWaitEvent(cs, ev, 0) == cudaSuccess &&
+              cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      const int64_t n0 = igp_launch_count();
+      const igp_status rec = enqueue(cs);
+      const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+      count_launches(-(igp_launch_count() - n0));  // recorded, not run: counted when the graph runs
+      ok = rec == IGP_OK && ec == cudaSuccess && graph &&
+           cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess && cudaGraphLaunch(exec, cs) == cudaSuccess &&
+           cudaEventRecord(ev, cs) == cudaSuccess && cudaStreamWaitEvent(s, ev, 0) == cudaSuccess;
+      if (ok) {
+        count_launches(8 * ((N + st.batch - 1) / st.batch));
+        ran = true;
+      }
+    }
+    cudaGetLastError();
+    if (exec) cudaGraphExecDestroy(exec);  // freed when the launch completes
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) {
+      cudaStreamSynchronize(cs);
+      cudaStreamDestroy(cs);
+    }
+    if (ev) cudaEventDestroy(ev);
   }
+  if (!ran && (e = enqueue(s)) != IGP_OK) return done(e);
   if (labels && labels != lab_out &&
       cudaMemcpyAsync(labels, lab_out, (size_t)N * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return done(cuda_status(cudaGetLastError(), "cudaMemcpyAsync", __FILE__, __LINE__));

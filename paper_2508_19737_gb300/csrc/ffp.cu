@@ -443,6 +443,32 @@ __device__ __forceinline__ int qfix(float t) {
   return (int)(__float_as_uint(__fmaf_rn(t, kQScale, kQMagic)) - kQMagicBits);
 }
 
+// Eq. 4 for the VPL values of one row that a lane owns, after its neighbours were added up:
+//   sv  : the row's stored values s_i (= dinv_i t_i; t_i when dinv_i = 0), unpacked
+//   acc : sum over neighbours j of their stored values s_j
+//   mu, is : the column means and 1/std of T^(l-1) (the previous layer's ZNorm)
+// gives T^(l)_i = tanh(theta z_i + alpha dinv_i (sum_j dinv_j z_j)) with z = (t - mu) is, adds t and
+// t^2 to the exact column sums, and returns the values to store (dinv_i t, or t). Every layer kernel
+// uses this one function, so all of them compute a row in the same way.
+template <typename S, int VPL>
+__device__ __forceinline__ void layer_epilogue(const float (&sv)[VPL], const float (&acc)[VPL], float di, float wi,
+                                               const float* mu, const float* is, float alpha, float theta,
+                                               long long (&qs)[VPL], long long (&qq)[VPL], float (&o)[VPL]) {
+  const bool scaled = di > 0.0f;
+  const float rdi = scaled ? __frcp_rn(di) : 1.0f;
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) {
+    const float ti = scaled ? sv[v] * rdi : sv[v];
+    const float zi = (ti - mu[v]) * is[v];
+    const float agg = is[v] * fmaf(-mu[v], wi, acc[v]);
+    const float y = fmaf(theta, zi, alpha * di * agg);
+    const float t = tanh_for<S>(y);
+    qs[v] += qfix(t);
+    qq[v] += qfix(__fmul_rn(t, t));
+    o[v] = scaled ? di * t : t;
+  }
+}
+
 // Heavy rows: in the single-graph layer, rows of at least layer_heavy_min(G) entries (they
 // lead the degree order) are gathered by the whole warp, one row per tile, so that no warp is
 // left with a chain of trips longer than the rest of the layer: the row's entries are cut into
@@ -640,22 +666,8 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer(
     if (r >= 0 && (!heavy || grp == 0)) {
       float sv[VPL];
       RW::unpack(cur.self, sv);
-      const bool scaled = cur.di > 0.0f;
-      const float rdi = scaled ? __frcp_rn(cur.di) : 1.0f;
       float o[VPL];
-#pragma unroll
-      for (int v = 0; v < VPL; ++v) {
-        const int cidx = lig * VPL + v;
-        const float mu = s_mu[cidx], is = s_is[cidx];
-        const float ti = scaled ? sv[v] * rdi : sv[v];
-        const float zi = (ti - mu) * is;
-        const float agg = is * fmaf(-mu, cur.wi, acc[v]);
-        const float y = fmaf(theta, zi, alpha * cur.di * agg);
-        const float t = tanh_for<S>(y);
-        qs[v] += qfix(t);
-        qq[v] += qfix(__fmul_rn(t, t));
-        o[v] = scaled ? cur.di * t : t;
-      }
+      layer_epilogue<S, VPL>(sv, acc, cur.di, cur.wi, s_mu + lig * VPL, s_is + lig * VPL, alpha, theta, qs, qq, o);
       store_chunk_cs(Tout + (int64_t)r * D, o);
     }
     r = r_n;
@@ -1009,22 +1021,8 @@ __global__ void __launch_bounds__(kLayerThreads, 2) k_layer_tma(
     if (r >= 0) {
       float sv[VPL];
       RW::unpack(cur.self, sv);
-      const bool scaled = cur.di > 0.0f;
-      const float rdi = scaled ? __frcp_rn(cur.di) : 1.0f;
       float o[VPL];
-#pragma unroll
-      for (int v = 0; v < VPL; ++v) {
-        const int cidx = lig * VPL + v;
-        const float mu = s_mu[cidx], is = s_is[cidx];
-        const float ti = scaled ? sv[v] * rdi : sv[v];
-        const float zi = (ti - mu) * is;
-        const float agg = is * fmaf(-mu, cur.wi, acc[v]);
-        const float y = fmaf(theta, zi, alpha * cur.di * agg);
-        const float t = tanh_for<S>(y);
-        qs[v] += qfix(t);
-        qq[v] += qfix(__fmul_rn(t, t));
-        o[v] = scaled ? cur.di * t : t;
-      }
+      layer_epilogue<S, VPL>(sv, acc, cur.di, cur.wi, s_mu + lig * VPL, s_is + lig * VPL, alpha, theta, qs, qq, o);
       store_chunk_cs(Tout + (int64_t)r * D, o);
     }
     r = r_n;
@@ -1353,22 +1351,8 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer_bat
     if (r >= 0) {
       float sv[VPL];
       RW::unpack(cur.self, sv);
-      const bool scaled = cur.di > 0.0f;
-      const float rdi = scaled ? __frcp_rn(cur.di) : 1.0f;
       float o[VPL];
-#pragma unroll
-      for (int v = 0; v < VPL; ++v) {
-        const int cidx = lig * VPL + v;
-        const float mu = s_mu[warp][cidx], is = s_is[warp][cidx];
-        const float ti = scaled ? sv[v] * rdi : sv[v];
-        const float zi = (ti - mu) * is;
-        const float agg = is * fmaf(-mu, cur.wi, acc[v]);
-        const float y = fmaf(theta, zi, alpha * cur.di * agg);
-        const float t = tanh_for<S>(y);
-        qs[v] += qfix(t);
-        qq[v] += qfix(__fmul_rn(t, t));
-        o[v] = scaled ? cur.di * t : t;
-      }
+      layer_epilogue<S, VPL>(sv, acc, cur.di, cur.wi, s_mu[warp] + lig * VPL, s_is[warp] + lig * VPL, alpha, theta, qs, qq, o);
       store_chunk_cs(Tout + (int64_t)r * D, o);
     }
     r = r_n;
@@ -1438,7 +1422,9 @@ __device__ __forceinline__ bool wait_ready(const int* ready, int g, int l, int* 
       }
     }
   }
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();  // the other lanes' later reads are ordered after lane 0's acquire
+  return ok != 0;
 }
 
 template <int D, typename S>
@@ -1500,7 +1486,9 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_ffp_batch
         const unsigned n = (unsigned)(goff[cur_g + 1] - goff[cur_g]) + ((withhold && cur_g == 0) ? 1u : 0u);
         last = atomicAdd(rows_done + cur_g, rows) + rows == n;
       }
-      if (__shfl_sync(0xffffffffu, last, 0)) {
+      last = __shfl_sync(0xffffffffu, last, 0);
+      __syncwarp();  // every lane's reads of the sums are ordered after lane 0's count update
+      if (last) {
         __threadfence();
         const double n = (double)(goff[cur_g + 1] - goff[cur_g]);
         float* so = stats + ((int64_t)(cur_l & 1) * G + cur_g) * 2 * D;
@@ -1649,22 +1637,8 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_ffp_batch
     if (r >= 0) {
       float sv[VPL];
       Raw<S>::unpack(cur.self, sv);
-      const bool scaled = cur.di > 0.0f;
-      const float rdi = scaled ? __frcp_rn(cur.di) : 1.0f;
       float o[VPL];
-#pragma unroll
-      for (int v = 0; v < VPL; ++v) {
-        const int cidx = lig * VPL + v;
-        const float mu = s_mu[warp][cidx], is = s_is[warp][cidx];
-        const float ti = scaled ? sv[v] * rdi : sv[v];
-        const float zi = (ti - mu) * is;
-        const float agg = is * fmaf(-mu, cur.wi, acc[v]);
-        const float y = fmaf(theta, zi, alpha * cur.di * agg);
-        const float t = tanh_for<S>(y);
-        qs[v] += qfix(t);
-        qq[v] += qfix(__fmul_rn(t, t));
-        o[v] = scaled ? cur.di * t : t;
-      }
+      layer_epilogue<S, VPL>(sv, acc, cur.di, cur.wi, s_mu[warp] + lig * VPL, s_is[warp] + lig * VPL, alpha, theta, qs, qq, o);
       store_chunk_cs(Tout + (int64_t)r * D + lig * VPL, o);
     }
     rows += __popc(__ballot_sync(0xffffffffu, lig == 0 && r >= 0));

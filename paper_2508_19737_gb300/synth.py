@@ -332,6 +332,14 @@ STREAM_WORKLOADS = {
 }
 
 
+# The clusterer on the FFP output of a graph shaped like the paper's 1M-node benchmark graphs, at
+# Table II's static setting for N = 1M (tau = -80, L = 60, d = 32); threshold 1.0, batches of 4,096.
+CLUSTER_WORKLOADS = {
+    "challenge-cluster-1m": dict(N=1_000_000, seed=4, tau=-80.0, L=60, d=32, storage="f32", threshold=1.0,
+                                 batch=4096),
+}
+
+
 def serve_graph(params, k):
     """Increments of graph k of a served stream: list of (src, dst, N_t)."""
     ss = np.random.SeedSequence(params["seed"])
