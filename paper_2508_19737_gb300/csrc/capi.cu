@@ -485,6 +485,8 @@ static void batch_release(igp_batch* b) {
   void* ptrs[] = {b->row_ptr, b->col, b->row_graph, b->perm, b->pgraph, b->goff, b->seeds_dev, b->dinv, b->ws};
   for (void* q : ptrs)
     if (q) cudaFreeAsync(q, 0);
+  for (auto& kv : b->chunks)
+    if (kv.second.start) cudaFreeAsync(kv.second.start, 0);
   cudaStreamSynchronize(0);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->cs) cudaStreamDestroy(b->cs);
@@ -555,7 +557,7 @@ igp_status igp_batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const
     return IGP_E_INVAL;
   }
   if (o.x_in || o.chunk_cols != 0 || (o.gather != IGP_GATHER_AUTO && o.gather != IGP_GATHER_LSU) ||
-      (o.reserved_test != 0 && (o.reserved_test < 2 || o.reserved_test > 5)) || o.out_row_begin != 0) {
+      (o.reserved_test != 0 && (o.reserved_test < 2 || o.reserved_test > 7)) || o.out_row_begin != 0) {
     set_error("igp_batch_embed: x_in, chunk_cols, TMA gathers and out_row_begin are not supported for batches");
     return IGP_E_INVAL;
   }

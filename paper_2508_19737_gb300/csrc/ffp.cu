@@ -1183,6 +1183,50 @@ __global__ void k_batch_pack(const PackSrc* __restrict__ src, int32_t G, int32_t
   }
 }
 
+// Work-balanced chunks of the processing order. Warps claim chunks of consecutive warp tiles. A
+// tile costs about its longest row (its row groups gather in lockstep) plus a fixed part, and each
+// graph's rows come by decreasing degree, so chunks of equal length would differ in cost by orders
+// of magnitude (a graph's first chunk holds its hubs). Tile t weighs w_t = (largest degree in the
+// tile) + kTileWeight; with W_t the sum of the weights before tile t, a chunk is a run of tiles with
+// equal floor(W_t / W), W set so that chunks hold `mean` positions on average. A chunk then costs
+// at most W plus its last tile. (The sum of the weights is below nnz + 4 P < 2^31.)
+constexpr int kTileWeight = 4;
+
+__global__ void k_tile_weight(const int32_t* __restrict__ perm, const int32_t* __restrict__ row_ptr, int64_t T,
+                              int gpw, int* __restrict__ w) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x) {
+    int m = 0;
+    for (int k = 0; k < gpw; ++k) {
+      const int r = perm[t * gpw + k];
+      if (r >= 0) m = max(m, row_ptr[r + 1] - row_ptr[r]);
+    }
+    w[t] = m + kTileWeight;
+  }
+}
+
+// f[t] = 1 where tile t starts a chunk (ex: exclusive prefix sums of w).
+__global__ void k_chunk_flags(const int* __restrict__ w, const int* __restrict__ ex, int64_t T, int gpw, int mean,
+                              int* __restrict__ f) {
+  const int64_t total = (int64_t)ex[T - 1] + w[T - 1];
+  const int64_t want = max((int64_t)1, (T * gpw + mean - 1) / mean);  // chunks wanted
+  const int64_t W = max((int64_t)1, (total + want - 1) / want);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x)
+    f[t] = (t == 0 || ex[t] / W != ex[t - 1] / W) ? 1 : 0;
+}
+
+// start[fx[t]] = t gpw for every tile t that starts a chunk; start[K] = T gpw = P and *count = K.
+__global__ void k_chunk_starts(const int* __restrict__ f, const int* __restrict__ fx, int64_t T, int gpw,
+                               int32_t* __restrict__ start, int* __restrict__ count) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x) {
+    if (f[t]) start[fx[t]] = (int32_t)(t * gpw);
+    if (t == T - 1) {
+      const int K = fx[t] + f[t];
+      start[K] = (int32_t)(T * gpw);
+      *count = K;
+    }
+  }
+}
+
 // Theta for packed row i: the draw of row i - goff[g] of graph g = row_graph[i] with seeds[g].
 template <typename S>
 __global__ void k_theta_batch(const uint64_t* __restrict__ seeds, const int32_t* __restrict__ row_graph,
@@ -1224,7 +1268,8 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer_bat
     const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, const float* __restrict__ dinv,
     const float* __restrict__ wsum, const int32_t* __restrict__ perm, const int32_t* __restrict__ pgraph, int64_t P,
     const S* __restrict__ Tin, S* __restrict__ Tout_all, const float* __restrict__ stats_in,
-    unsigned long long* __restrict__ gsum, unsigned* __restrict__ chunk_ctr, float alpha, float theta, int chunk) {
+    unsigned long long* __restrict__ gsum, unsigned* __restrict__ chunk_ctr, float alpha, float theta,
+    const int32_t* __restrict__ cst, const int* __restrict__ nchunk) {
   using RW = Raw<S>;
   using RT = typename RW::T;
   constexpr int VPL = Store<S>::VPL;
@@ -1239,22 +1284,28 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer_bat
   const int grp = lane / G, lig = lane % G;
   S* __restrict__ Tout = Tout_all + lig * VPL;
   const uint64_t pol_first = evict_first_policy();
-  // chunks claimed by this warp, one claim ahead of use
-  auto claim = [&]() -> int64_t {
+  // chunks claimed by this warp, one claim ahead of use; chunk k holds the positions
+  // [cst[k], cst[k+1]) (work-balanced, see k_tile_weight), k = K stands for the end (cst[K] = P)
+  const int K = __ldg(nchunk);
+  auto claim = [&]() -> int {
     unsigned c = 0;
     if (lane == 0) c = atomicAdd(chunk_ctr, 1u);
-    return (int64_t)__shfl_sync(0xffffffffu, c, 0) * chunk;
+    return (int)min(__shfl_sync(0xffffffffu, c, 0), (unsigned)K);
   };
-  int64_t next_chunk = claim();
-  auto next_pos = [&](int64_t p) -> int64_t {
-    const int64_t q = p + GPW;
-    if (q % chunk) return q;
-    const int64_t c = next_chunk;
-    next_chunk = claim();
-    return c;
+  int kn = claim();
+  const int64_t p0 = __ldg(cst + kn);
+  int64_t fe = __ldg(cst + kn + (kn < K ? 1 : 0));  // end of the chunk of the newest position
+  kn = claim();
+  // the position after q (the newest one): the next of its chunk, else the start of the chunk
+  // claimed ahead (claims only grow, so once the end is returned it is returned again)
+  auto next_pos = [&](int64_t q) -> int64_t {
+    q += GPW;
+    if (q < fe) return q;
+    const int k = kn;
+    kn = claim();
+    fe = __ldg(cst + k + (k < K ? 1 : 0));
+    return __ldg(cst + k);
   };
-  const int64_t p0 = next_chunk;
-  next_chunk = claim();
 
   long long qs[VPL], qq[VPL];
 #pragma unroll
@@ -1366,13 +1417,15 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_layer_bat
 
 // ------------------------------------------------------------------ batches, one persistent launch
 // All L layers of a batch in one cooperative launch (every CTA resident). Warps claim chunks of a
-// queue of (layer, position) pairs, layer-major; a tile of graph g at layer l needs g's layer l-1
-// complete, which the warp that completes it announces: every warp adds its column sums and its
-// row count for (g, l) when it leaves (g, l); the one whose count completes g's rows forms g's
-// mean and 1/std, clears the sums and the count, and publishes ready[g] = l. So a graph moves to
-// its next layer as soon as its own rows are done, without a barrier over the batch. Claims are
-// in queue order and every earlier chunk is held by a resident warp, so every wait ends; each is
-// still bounded (about a second of globaltimer), after which the warp sets *err and returns.
+// queue of (layer, chunk of the order) pairs, layer-major; a tile of graph g at layer l needs g's
+// layer l-1 complete, which the warp that completes it announces: every warp adds its column sums
+// and its row count for (g, l) when it leaves (g, l); the one whose count completes g's rows forms
+// g's mean and 1/std, clears the sums and the count, and publishes ready[g] = l. So a graph moves
+// to its next layer as soon as its own rows are done, without a barrier over the batch. Every wait
+// ends: a warp waits only for chunks earlier in the queue than the one it enters, and the earliest
+// unfinished chunk is held by a resident warp (as its current chunk, or as the one it claimed
+// ahead after a finished one) whose own wait, if any, is for chunks that are all finished. Each
+// wait is still bounded (about a second of globaltimer), after which the warp sets *err and returns.
 // Rows of T written in this launch are read through L2 only (ld.cg): L1 is not coherent with
 // other SMs' stores within one launch.
 template <typename S>
@@ -1434,7 +1487,7 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_ffp_batch
     int L, S* __restrict__ T0, S* __restrict__ T1, float* __restrict__ stats, unsigned long long* __restrict__ gsum,
     unsigned* __restrict__ rows_done, int* __restrict__ ready, const int32_t* __restrict__ goff,
     unsigned long long* __restrict__ qctr, int* __restrict__ err, int32_t G, float alpha, float theta, int ddof,
-    int chunk, int withhold) {
+    const int32_t* __restrict__ cst, const int* __restrict__ nchunk, int withhold) {
   using RT = typename Raw<S>::T;
   constexpr int VPL = Store<S>::VPL;
   constexpr int GW = D / VPL;  // lanes per row
@@ -1447,11 +1500,12 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_ffp_batch
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane / GW, lig = lane % GW;
   const uint64_t pol_first = evict_first_policy();
-  const int64_t Q = (int64_t)L * P;
+  const int K = __ldg(nchunk);  // work-balanced chunks of the order: chunk k = [cst[k], cst[k+1])
+  const int64_t Q = (int64_t)L * K;
   auto claim = [&]() -> int64_t {
     unsigned long long c = 0;
     if (lane == 0) c = atomicAdd(qctr, 1ull);
-    return (int64_t)__shfl_sync(0xffffffffu, c, 0) * chunk;
+    return (int64_t)__shfl_sync(0xffffffffu, c, 0);
   };
 
   long long qs[VPL], qq[VPL];
@@ -1533,40 +1587,36 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_ffp_batch
   };
   const S* __restrict__ Tin = T0;
   S* __restrict__ Tout = T1;
-  // A queue position as (layer - 1, position in the order); converted from the claimed chunk's
-  // queue index once per chunk (one 64-bit division), then advanced by adding GPW.
+  // A queue position: layer - 1, position in the order and the end of its chunk; the claimed queue
+  // index qq = (layer - 1) K + chunk is converted once per chunk (one 64-bit division), then the
+  // position is advanced by adding GPW.
   struct Pos {
-    int64_t l, p;  // l = Q marks the end of the queue
+    int64_t l, p, e;  // l = L marks the end of the queue
   };
   auto at = [&](int64_t qq) -> Pos {
-    if (qq >= Q) return Pos{(int64_t)L, 0};
-    const int64_t l = qq / P;
-    return Pos{l, qq - l * P};
+    if (qq >= Q) return Pos{(int64_t)L, 0, 0};
+    const int64_t l = qq / K;
+    const int k = (int)(qq - l * K);
+    return Pos{l, __ldg(cst + k), __ldg(cst + k + 1)};
   };
-  // row data of the tile at position x (its T row read through L2)
+  // row data of the tile at position x: the parts that do not change during the launch (row,
+  // entry range, degree factors), which may be read at any time
   auto fetch = [&](const Pos& x, RowData& rd) {
     rd.r = __ldg(perm + x.p + grp);
     rd.b = rd.e = 0;
     rd.di = rd.wi = 0.0f;
-    rd.self = Raw<S>::zero();
     if (rd.r >= 0) {
       rd.b = __ldg(row_ptr + rd.r);
       rd.e = __ldg(row_ptr + rd.r + 1);
       rd.di = __ldg(dinv + rd.r);
       rd.wi = __ldg(wsum + rd.r);
-      rd.self = RawCg<S>::load(Tin + (int64_t)rd.r * D + lig * VPL);
     }
+  };
+  // the row's own value of T^(l-1) (through L2), read only once its segment's wait is over
+  auto fetch_self = [&](RowData& rd) {
+    rd.self = rd.r >= 0 ? RawCg<S>::load(Tin + (int64_t)rd.r * D + lig * VPL) : Raw<S>::zero();
   };
   auto graph_of = [&](const Pos& x) -> int { return __ldg(pgraph + x.p / kBatchAlign); };
-  // the next position of the same chunk
-  auto step = [&](const Pos& x) -> Pos {
-    Pos y{x.l, x.p + GPW};
-    if (y.p == P) {
-      y.l += 1;
-      y.p = 0;
-    }
-    return y;
-  };
   // enter the segment (layer x.l + 1, graph g): flush the last one, wait for the graph's previous
   // layer, load its statistics and pick the layer's buffers; false if a wait gave up
   auto enter = [&](const Pos& x, int g) -> bool {
@@ -1586,10 +1636,19 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_ffp_batch
     return true;
   };
 
-  // Chunks are claimed when a warp is ready to start them (a chunk claimed ahead would hold back the
-  // completion of its graphs while the warp finishes its current chunk).
+  // Chunks are claimed one ahead of use, so that the next tile's row data and column indices are
+  // read during the current tile's gathers, across chunk boundaries too. (Its own row of T is read
+  // there only when it continues the current segment; otherwise after the segment's wait.) The
+  // chunk held ahead delays its graphs' completion by at most one chunk, which work-balanced chunks
+  // keep short against the layer of queue between a graph's chunks of two consecutive layers.
   Pos x = at(claim());
-  int left = chunk / GPW;  // tiles of the current chunk, this one included
+  Pos xa = at(claim());  // the chunk claimed ahead
+  auto next_of = [&](const Pos& y) -> Pos {  // the position after y (claims only grow: the end stays)
+    if (y.p + GPW < y.e) return Pos{y.l, y.p + GPW, y.e};
+    const Pos z = xa;
+    if (z.l < L) xa = at(claim());
+    return z;
+  };
   if (x.l >= L) {
     flush();
     return;
@@ -1598,21 +1657,16 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_ffp_batch
   if (!enter(x, gx)) return;
   RowData cur;
   fetch(x, cur);
+  fetch_self(cur);
   int jw[IPL];
   load_idx(jw, cur.b, cur.e);
   while (true) {
-    // the next tile of the chunk is read during this tile's gathers when it belongs to the same
-    // segment (its dependency is then already met); otherwise after the switch
-    const bool in_chunk = left > 1;
-    Pos xn = x;
-    int gn = -1;
-    if (in_chunk) {
-      xn = step(x);
-      gn = xn.l < L ? graph_of(xn) : -1;
-    }
-    const bool same = in_chunk && xn.l == x.l && gn == gx;
+    const Pos xn = next_of(x);
+    const int gn = xn.l < L ? graph_of(xn) : -1;
+    const bool same = xn.l == x.l && gn == gx;  // the next tile continues the segment
     RowData nxt;
-    if (same) fetch(xn, nxt);
+    if (xn.l < L) fetch(xn, nxt);
+    if (same) fetch_self(nxt);
     const int mtrip = __reduce_max_sync(0xffffffffu, (cur.e - cur.b + C - 1) / C);
     float acc[VPL];
 #pragma unroll
@@ -1632,7 +1686,7 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_ffp_batch
 #pragma unroll
       for (int k = 0; k < IPL; ++k) jw[k] = jn[k];
     }
-    if (same) load_idx(jw, nxt.b, nxt.e);
+    if (xn.l < L) load_idx(jw, nxt.b, nxt.e);
     const int r = cur.r;
     if (r >= 0) {
       float sv[VPL];
@@ -1642,23 +1696,14 @@ __global__ void __launch_bounds__(kLayerThreads, IGP_LAYER_MIN_CTAS) k_ffp_batch
       store_chunk_cs(Tout + (int64_t)r * D + lig * VPL, o);
     }
     rows += __popc(__ballot_sync(0xffffffffu, lig == 0 && r >= 0));
-    if (in_chunk) {
-      --left;
-      x = xn;
-      gx = gn;
-    } else {
-      left = chunk / GPW;
-      x = at(claim());
-      gx = x.l < L ? graph_of(x) : -1;
-    }
+    x = xn;
+    gx = gn;
     if (x.l >= L) break;
-    if (same) {
-      cur = nxt;
-    } else {
+    if (!same) {
       if (!enter(x, gx)) return;
-      fetch(x, cur);
-      load_idx(jw, cur.b, cur.e);
+      fetch_self(nxt);
     }
+    cur = nxt;
   }
   flush();
 }
@@ -1903,12 +1948,12 @@ struct BatchCfg {
 
 template <int D, typename S>
 igp_status batch_layer_launch(const igp_batch* b, const void* Tin, void* Tout, const float* st_in,
-                              unsigned long long* gsum, float alpha, float theta, int grid, int chunk,
-                              cudaStream_t s) {
+                              unsigned long long* gsum, float alpha, float theta, int grid, const int32_t* cst,
+                              const int* nchunk, cudaStream_t s) {
   k_layer_batch<D, S><<<grid, kLayerThreads, 0, s>>>(b->row_ptr, b->col, b->dinv, b->wsum, b->perm, b->pgraph,
                                                      b->P, (const S*)Tin, (S*)Tout, st_in, gsum,
                                                      (unsigned*)(gsum + (int64_t)b->G * 2 * D), alpha, theta,
-                                                     chunk);
+                                                     cst, nchunk);
   return after_launch("k_layer_batch");
 }
 
@@ -1922,7 +1967,9 @@ struct PersistArgs {
   int* ready;
   unsigned long long* qctr;
   int* err;
-  int L, ddof, chunk, grid, withhold;
+  const int32_t* cst;  // chunk table of the order: starts [K + 1], and K
+  const int* nchunk;
+  int L, ddof, grid, withhold;
   float alpha, theta;
 };
 
@@ -1958,9 +2005,11 @@ igp_status batch_persist_launch(const igp_batch* b, const PersistArgs& a, cudaSt
   int* err = a.err;
   int32_t G = b->G;
   float alpha = a.alpha, theta = a.theta;
-  int ddof = a.ddof, chunk = a.chunk, withhold = a.withhold;
+  int ddof = a.ddof, withhold = a.withhold;
+  const int32_t* cst = a.cst;
+  const int* nchunk = a.nchunk;
   void* args[] = {&row_ptr, &col, &dinv, &wsum, &perm, &pgraph, &P, &L, &T0, &T1, &stats, &gsum, &rows_done,
-                  &ready, &goff, &qctr, &err, &G, &alpha, &theta, &ddof, &chunk, &withhold};
+                  &ready, &goff, &qctr, &err, &G, &alpha, &theta, &ddof, &cst, &nchunk, &withhold};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_ffp_batch_persistent<D, S>, dim3(a.grid),
                                               dim3(kLayerThreads), args, 0, s);
   if (e != cudaSuccess) {
@@ -2000,11 +2049,12 @@ igp_status batch_theta_launch(const igp_batch* b, int d, float xs, void* out, cu
 }
 
 struct BatchOps {
+  int gpw;  // rows per warp tile
   int (*per_sm)();
   int (*persist_per_sm)();
   igp_status (*persist)(const igp_batch*, const PersistArgs&, cudaStream_t);
   igp_status (*layer)(const igp_batch*, const void*, void*, const float*, unsigned long long*, float, float, int,
-                      int, cudaStream_t);
+                      const int32_t*, const int*, cudaStream_t);
   igp_status (*tail)(const igp_batch*, unsigned long long*, int, float*, cudaStream_t);
   igp_status (*output)(const igp_batch*, const void*, const float*, int, float*, cudaStream_t);
   igp_status (*theta)(const igp_batch*, int, float, void*, cudaStream_t);
@@ -2012,7 +2062,7 @@ struct BatchOps {
 
 template <int D, typename S>
 BatchOps batch_ops_for() {
-  return BatchOps{&BatchCfg<D, S>::per_sm, &persist_per_sm<D, S>, &batch_persist_launch<D, S>,
+  return BatchOps{32 / (D / Store<S>::VPL), &BatchCfg<D, S>::per_sm, &persist_per_sm<D, S>, &batch_persist_launch<D, S>,
                   &batch_layer_launch<D, S>, &batch_tail_launch<D, S>, &batch_output_launch<D, S>,
                   &batch_theta_launch<S>};
 }
@@ -2358,6 +2408,56 @@ igp_status batch_create(igp_graph* const* graphs, int32_t G, cudaStream_t s, igp
   return IGP_OK;
 }
 
+// The batch's chunk table for warp tiles of gpw rows and chunks of `mean` positions on average,
+// built on first use (stream-ordered) and kept with the batch.
+igp_status ensure_chunks(igp_batch* b, int gpw, int mean, cudaStream_t s, igp_batch::Chunks* out) {
+  const auto key = std::make_pair(gpw, mean);
+  auto it = b->chunks.find(key);
+  if (it != b->chunks.end()) {
+    *out = it->second;
+    return IGP_OK;
+  }
+  const int64_t T = b->P / gpw;  // P is a multiple of kBatchAlign, which gpw divides
+  void* p = nullptr;
+  IGP_TRY(dev_alloc(&p, (size_t)(T + 2) * 4, s));
+  igp_batch::Chunks c{(int32_t*)p, (int*)p + T + 1};
+  igp_status st = IGP_OK;
+  if (T == 0) {
+    if (cudaMemsetAsync(p, 0, 8, s) != cudaSuccess) st = cuda_status(cudaGetLastError(), "chunk table", __FILE__, __LINE__);
+  } else {
+    void* q = nullptr;
+    const int64_t ntile = (T + 8191) / 8192;
+    st = dev_alloc(&q, (size_t)(3 * T + ntile) * 4, s);
+    if (st == IGP_OK) {
+      int* w = (int*)q;
+      int* ex = w + T;
+      int* f = ex + T;
+      int* tmp = f + T;
+      const int blocks = (int)std::min<int64_t>((T + 255) / 256, (int64_t)num_sms() * 8);
+      k_tile_weight<<<blocks, 256, 0, s>>>(b->perm, b->row_ptr, T, gpw, w);
+      st = after_launch("k_tile_weight");
+      if (st == IGP_OK) st = exclusive_scan(w, ex, T, tmp, s);
+      if (st == IGP_OK) {
+        k_chunk_flags<<<blocks, 256, 0, s>>>(w, ex, T, gpw, mean, f);
+        st = after_launch("k_chunk_flags");
+      }
+      if (st == IGP_OK) st = exclusive_scan(f, w, T, tmp, s);  // w := index of each starting tile's chunk
+      if (st == IGP_OK) {
+        k_chunk_starts<<<blocks, 256, 0, s>>>(f, w, T, gpw, c.start, c.count);
+        st = after_launch("k_chunk_starts");
+      }
+      dev_free(q, s);
+    }
+  }
+  if (st != IGP_OK) {
+    dev_free(p, s);
+    return st;
+  }
+  b->chunks[key] = c;
+  *out = c;
+  return IGP_OK;
+}
+
 igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uint64_t* seeds, float* out_dev,
                        const igp_embed_opts& o, cudaStream_t s, bool capture) {
   BatchOps bo;
@@ -2425,7 +2525,8 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
   const double xs = o.x_scale > 0 ? o.x_scale : 1.0 / std::sqrt((double)d);
   // test hooks (reserved_test, the library's own tests only): 2 = the persistent plan with one row
   // of graph 0 withheld, so that its bounded waits run out; 3, 4 = the persistent plan (claims of
-  // 64 at one CTA per SM; of 256 at the resident maximum); 5 = one launch per layer (claims of 64)
+  // 64 at one CTA per SM; of 256 at the resident maximum); 5 = one launch per layer (claims of 64);
+  // 6, 7 = the persistent plan with claims of 64, 32 at the resident maximum
   const int withhold = o.reserved_test == 2 ? 1 : 0;
 
   IGP_TRY_CUDA(cudaMemcpyAsync(b->seeds_dev, seeds, (size_t)G * 8, cudaMemcpyHostToDevice, s));
@@ -2441,7 +2542,9 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
     const void* cur = T0;
     const float* st_prev = nullptr;
     if (pl.mode == 1 && L > 0) {
-      PersistArgs a{T0, T1, stats, gsum, rows_done, ready, qctr, err, L, o.znorm_ddof, pl.chunk,
+      igp_batch::Chunks ch;
+      IGP_TRY(ensure_chunks(b, bo.gpw, pl.chunk, q, &ch));
+      PersistArgs a{T0, T1, stats, gsum, rows_done, ready, qctr, err, ch.start, ch.count, L, o.znorm_ddof,
                     pl.ctas * num_sms(), withhold, (float)o.alpha, (float)o.theta};
       {
         PhaseTimer pt(pf, IGP_PHASE_LAYER, q);
@@ -2457,8 +2560,10 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
         void* dst = (cur == T0) ? T1 : T0;
         float* st = stats + (size_t)(l & 1) * G * 2 * d;
         PhaseTimer pt(pf, IGP_PHASE_LAYER, q);
-        IGP_TRY(bo.layer(b, cur, dst, st_prev, gsum, (float)o.alpha, (float)o.theta, grid_for(pl.chunk), pl.chunk,
-                         q));
+        igp_batch::Chunks ch;
+        IGP_TRY(ensure_chunks(b, bo.gpw, pl.chunk, q, &ch));
+        IGP_TRY(bo.layer(b, cur, dst, st_prev, gsum, (float)o.alpha, (float)o.theta, grid_for(pl.chunk), ch.start,
+                         ch.count, q));
         IGP_TRY(bo.tail(b, gsum, o.znorm_ddof, st, q));
         cur = dst;
         st_prev = st;
@@ -2471,15 +2576,16 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
   // Schedule tuner: on the first embedding at a (d, storage, mean-degree bucket) in this process,
   // every candidate plan runs one whole FFP of this batch, timed with CUDA events, and the
   // fastest is kept for the key (later batches with the same key reuse it). Candidates: one
-  // launch per layer with each claim size, and the persistent launch with claim sizes 64 and 256
-  // at one CTA per SM and at the resident maximum.
+  // launch per layer with each claim size (32, 64, 128, 256 positions on average), and the
+  // persistent launch at the resident maximum with claims of 32, 64 and 128 (the positions in flight
+  // are what its warps gather from at once: larger claims overflow L2).
   const int tkey = d * 2 + o.storage;
   igp_batch::Plan plan;
-  if (o.reserved_test >= 2 && o.reserved_test <= 5) {
+  if (o.reserved_test >= 2 && o.reserved_test <= 7) {
     const int t = o.reserved_test;
     plan.mode = t == 5 ? 0 : 1;
-    plan.chunk = t == 4 ? 256 : 64;
-    plan.ctas = t == 4 ? bo.persist_per_sm() : 1;
+    plan.chunk = t == 4 ? 256 : t == 7 ? 32 : 64;
+    plan.ctas = (t == 4 || t >= 6) ? bo.persist_per_sm() : 1;
   } else {
     if (!b->plan.count(tkey)) {
       const int dbucket = (int)std::lround(std::log2(std::max(1.0, (double)b->nnz / std::max(1, N))));
@@ -2499,9 +2605,10 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
         std::vector<igp_batch::Plan> cands;
         for (int c : kBatchChunks) cands.push_back(igp_batch::Plan{0, c, 1});
         const int pm = bo.persist_per_sm();
-        for (int c : {64, 256}) {
-          cands.push_back(igp_batch::Plan{1, c, 1});
-          if (pm > 1) cands.push_back(igp_batch::Plan{1, c, pm});
+        for (int c : {32, 64, 128}) cands.push_back(igp_batch::Plan{1, c, pm});
+        for (const auto& c : cands) {  // chunk tables first: not part of any plan's time
+          igp_batch::Chunks ch;
+          IGP_TRY(ensure_chunks(b, bo.gpw, c.chunk, s, &ch));
         }
         std::vector<cudaEvent_t> ev(2 * cands.size() + 2, nullptr);
         for (auto& e : ev) IGP_TRY_CUDA(cudaEventCreate(&e));
@@ -2541,6 +2648,10 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
     plan = b->plan[tkey];
   }
   const int chunk = plan.chunk;
+  {
+    igp_batch::Chunks ch;  // built here, before any capture, on first use
+    IGP_TRY(ensure_chunks(b, bo.gpw, chunk, s, &ch));
+  }
 
   auto enqueue = [&](cudaStream_t q, Profile* pf) -> igp_status { return enqueue_plan(q, pf, plan); };
 

@@ -131,6 +131,13 @@ struct igp_batch {
     int mode = 0, chunk = 64, ctas = 1;
   };
   std::map<int, Plan> plan;
+  // work-balanced chunks of the order, per (rows per warp tile, mean positions per chunk):
+  // start[0..K] (start[K] = P) and K on the device, in one allocation
+  struct Chunks {
+    int32_t* start = nullptr;
+    int* count = nullptr;
+  };
+  std::map<std::pair<int, int>, Chunks> chunks;
   std::string exec_key;
   int* err_host = nullptr;        // pinned copy of the device error word of the last persistent launch
   cudaEvent_t ev_err = nullptr;   // recorded after that copy
