@@ -97,6 +97,13 @@ typedef struct igp_embed_opts {
                            extracts the new nodes' rows (as each step of Alg. 2 does). The FFP and its statistics still
                            run over all N rows. With N (no rows) `out` may be NULL and the call is
                            stream-ordered as for a device output. igp_batch_embed takes only 0. */
+  int32_t host_async;  /* 0 (default): with a HOST `out`, the call returns once `out` holds the result.
+                          1: a page-locked (pinned) host `out` is filled in stream order and the call
+                          returns without waiting: the result is formed in device memory (a temporary
+                          of the output's size from the pool) and copied by a copy engine, so the copy
+                          overlaps kernels on other streams. Read `out` only after igp_graph_sync(g)
+                          (which also reports a device-side timeout) or after the stream has drained.
+                          Ignored for device and pageable host outputs. */
   const void* x_in;    /* NULL: Theta from `seed`. Else a DEVICE pointer to N x d row-major values in
                           the storage type, used as Z^(0) instead (not modified). */
   igp_profile* profile;/* NULL, or a profile that records per-phase device times of this call */
@@ -177,8 +184,9 @@ igp_status igp_degree_factors(igp_graph* g, double tau, double eps, float* dinv,
  * IGP_OK or IGP_E_CUDA. */
 igp_status igp_graph_sync(igp_graph* g);
 
-/* Release a graph and its device memory. NULL is a no-op. The memory is returned to the library's
- * pool in stream order after the last work issued on the handle; the call does not block. */
+/* Release a graph and its device memory. NULL is a no-op. The call waits until the last work issued
+ * on the handle has finished (its page-locked error word may be written until then); the device
+ * memory is returned to the library's pool in stream order after that work. */
 void igp_graph_free(igp_graph* g);
 
 /*
@@ -303,7 +311,7 @@ typedef struct igp_request {
   int32_t d;
   int32_t reserved0;
   uint64_t seed;
-  igp_embed_opts opts;  /* as for igp_embed; x_in and profile must be NULL */
+  igp_embed_opts opts;  /* as for igp_embed; x_in and profile must be NULL, host_async 0 */
   float* out;           /* HOST N x d fp32, written when the request is done; keep it valid until then */
 } igp_request;
 

@@ -62,6 +62,7 @@ class EmbedOpts(ctypes.Structure):
         ("gather", ctypes.c_int32),
         ("reserved_test", ctypes.c_int32),
         ("out_row_begin", ctypes.c_int32),
+        ("host_async", ctypes.c_int32),
         ("x_in", ctypes.c_void_p),
         ("profile", ctypes.c_void_p),
     ]
@@ -223,7 +224,8 @@ def alloc_count():
 
 
 def embed_opts(alpha=1.0, theta=0.1, eps=1e-3, x_scale=0.0, znorm_ddof=1, storage="f32", out_row_l2=False,
-               x_in=None, profile=None, chunk_cols=0, gather="auto", reserved_test=0, out_row_begin=0):
+               x_in=None, profile=None, chunk_cols=0, gather="auto", reserved_test=0, out_row_begin=0,
+               host_async=False):
     o = EmbedOpts()
     lib().igp_embed_opts_init(ctypes.byref(o))
     o.alpha, o.theta, o.eps, o.x_scale = alpha, theta, eps, x_scale
@@ -234,6 +236,7 @@ def embed_opts(alpha=1.0, theta=0.1, eps=1e-3, x_scale=0.0, znorm_ddof=1, storag
     o.gather = GATHER[gather] if isinstance(gather, str) else int(gather)
     o.reserved_test = int(reserved_test)
     o.out_row_begin = int(out_row_begin)
+    o.host_async = 1 if host_async else 0
     o.x_in = _ptr(x_in)
     o.profile = profile.handle if profile is not None else None
     return o

@@ -214,6 +214,7 @@ void igp_embed_opts_init(igp_embed_opts* o) {
   o->storage = IGP_STORE_F32;
   o->out_row_l2 = 0;
   o->out_row_begin = 0;
+  o->host_async = 0;
   o->x_in = nullptr;
   o->profile = nullptr;
 }
@@ -418,7 +419,8 @@ igp_status igp_embed(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t se
   }
   if (!std::isfinite(tau) || L < 0 || L > 10000 || !std::isfinite(o.alpha) || !std::isfinite(o.theta) ||
       !(o.eps > 0) || !std::isfinite(o.eps) || (o.znorm_ddof != 0 && o.znorm_ddof != 1) ||
-      (o.storage != IGP_STORE_F32 && o.storage != IGP_STORE_BF16) || !std::isfinite(o.x_scale)) {
+      (o.storage != IGP_STORE_F32 && o.storage != IGP_STORE_BF16) || !std::isfinite(o.x_scale) ||
+      (o.host_async != 0 && o.host_async != 1)) {
     set_error("igp_embed: invalid tau, L or options");
     return IGP_E_INVAL;
   }
@@ -454,6 +456,20 @@ igp_status igp_embed(igp_graph* g, double tau, int32_t L, int32_t d, uint64_t se
   void* host_alias = on_device ? nullptr : pinned_alias(out);
   if (on_device) {
     st = run_ffp(g, tau, L, d, seed, bytes ? out : nullptr, o, s);
+  } else if (host_alias && o.host_async) {
+    // page-locked host output, asynchronous: the result is formed in device memory and copied by a
+    // copy engine in stream order, so the copy overlaps kernels of other streams (the output
+    // kernel writing across the host link would hold the SMs for as long); igp_graph_sync waits
+    void* tmp = nullptr;
+    IGP_TRY(dev_alloc(&tmp, bytes, s));
+    st = run_ffp(g, tau, L, d, seed, (float*)tmp, o, s);
+    if (st == IGP_OK) {
+      const cudaError_t e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, s);
+      if (e != cudaSuccess) st = cuda_status(e, "copy out", __FILE__, __LINE__);
+    }
+    dev_free(tmp, s);
+    if (st == IGP_OK) st = graph_mark(g, s);
+    return st;
   } else if (host_alias) {  // page-locked host output: written by the output kernel itself
     st = run_ffp(g, tau, L, d, seed, (float*)host_alias, o, s);
     if (st == IGP_OK && cudaStreamSynchronize(s) != cudaSuccess)

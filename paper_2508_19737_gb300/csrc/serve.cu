@@ -450,8 +450,10 @@ void igp_server_destroy(igp_server* sv) {
 igp_status igp_submit(igp_server* sv, const igp_request* r, uint64_t* ticket) {
   clear_error();
   if (!sv || !r || !ticket || !r->out || r->N < 1 || r->M < 0 || (r->M > 0 && (!r->src || !r->dst)) ||
-      (r->kind != IGP_REQ_EMBED && r->kind != IGP_REQ_APPEND) || r->opts.x_in || r->opts.profile) {
-    set_error("igp_submit: invalid request (kind, N, M, edges, out; opts.x_in and opts.profile must be NULL)");
+      (r->kind != IGP_REQ_EMBED && r->kind != IGP_REQ_APPEND) || r->opts.x_in || r->opts.profile ||
+      r->opts.host_async) {
+    set_error("igp_submit: invalid request (kind, N, M, edges, out; opts.x_in and opts.profile must be NULL, "
+              "opts.host_async 0)");
     return IGP_E_INVAL;
   }
   Req* q = new (std::nothrow) Req();

@@ -237,6 +237,37 @@ def test_pinned_host_output_equals_device_output(api):
     gr.free()
 
 
+def test_host_async_output_equals_synchronous_output(api):
+    """opts.host_async: the call returns once the work is enqueued and a page-locked output is
+    filled in stream order (through a device temporary and a copy engine); after
+    igp_graph_sync it holds the synchronous result bit for bit. Two graphs on two streams are in
+    flight at once, as in a pipelined caller; a pageable output ignores the option."""
+    import torch
+    gs = [synth.dcsbm(30011, 20, 24, 2.4, 5, seed=12), synth.dcsbm(20011, 16, 20, 2.5, 5, seed=13)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for storage in ("f32", "bf16"):
+        refs, grs, outs = [], [], []
+        for g in gs:
+            gr = api.graph_build(g.src, g.dst, g.N)
+            ref = torch.empty((g.N, 64), dtype=torch.float32, device="cuda")
+            api.embed(gr, -0.5, 6, 64, 4, out=ref, storage=storage)
+            refs.append(ref.cpu().numpy())
+            grs.append(gr)
+        torch.cuda.synchronize()
+        for k, (g, gr) in enumerate(zip(gs, grs)):
+            out = torch.full((g.N, 64), -1.0, dtype=torch.float32).pin_memory()
+            api.embed(gr, -0.5, 6, 64, 4, out=out, storage=storage, host_async=True, stream=streams[k])
+            outs.append(out)
+        for gr, out, ref in zip(grs, outs, refs):
+            gr.sync()
+            assert np.array_equal(out.numpy(), ref)
+        pageable = np.full((gs[0].N, 64), -1.0, dtype=np.float32)
+        api.embed(grs[0], -0.5, 6, 64, 4, out=pageable, storage=storage, host_async=True)
+        assert np.array_equal(pageable, refs[0])
+        for gr in grs:
+            gr.free()
+
+
 def test_bf16_against_bf16_emulating_oracle(api):
     g = synth.dcsbm(20011, 32, 25, 2.5, 4, seed=7, dirichlet_alpha=2.0)
     got, ref, (rp, col, X, _) = _ffp_case(api, g.src, g.dst, g.N, 64, -0.5, 10, storage="bf16")

@@ -107,6 +107,9 @@ def test_cancel_and_failures(api):
     with pytest.raises(api.IgpError) as e:  # larger than any device
         sv.submit(g.src, g.dst, 2 ** 31 - 1, -0.5, 3, 128, 0, out=np.empty((1, 128), np.float32))
     assert e.value.status == api.IGP_E_NOMEM
+    with pytest.raises(api.IgpError) as e:  # a served result is final when its request completes
+        sv.submit(g.src, g.dst, g.N, -0.5, 3, 32, 0, host_async=True)
+    assert e.value.status == api.IGP_E_INVAL
     ok = sv.submit(g.src, g.dst, g.N, -0.5, 3, 32, 0)  # the server still serves
     assert sv.wait(ok)[0] == "done"
     st = sv.stats()
