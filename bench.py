@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--workload", default="dcsbm-2m", choices=sorted(synth.WORKLOADS) + sorted(synth.BATCH_WORKLOADS)
                    + sorted(synth.SERVE_WORKLOADS) + sorted(synth.STREAM_WORKLOADS)
                    + sorted(synth.CLUSTER_WORKLOADS))
-    p.add_argument("--slots", type=int, default=8, help="concurrent requests of the served stream")
+    p.add_argument("--slots", type=int, default=16, help="concurrent requests of the served stream")
     p.add_argument("--batch-rows", type=int, default=0,
                    help="served graphs with fewer nodes share batched FFPs (0: every slot embeds its own)")
     p.add_argument("--d", type=int, default=None, help="override the workload's embedding width")

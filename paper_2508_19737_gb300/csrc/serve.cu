@@ -251,7 +251,14 @@ void embed_batch(const std::vector<Req*>& qs, cudaStream_t s) {
 
 void embed_alone(Req* q, cudaStream_t s) {
   igp_request& r = q->r;
-  const igp_status st = igp_embed(q->g, r.tau, r.L, r.d, r.seed, r.out, &r.opts, s);
+  // A page-locked output is formed in device memory (the staging the admission estimate counts)
+  // and copied by a copy engine, which overlaps the other slots' kernels; written by the output
+  // kernel across the host link instead, it would hold the SMs for the whole transfer. The slot
+  // waits for the copy, so the result is final when the request completes.
+  igp_embed_opts o = r.opts;
+  o.host_async = 1;
+  igp_status st = igp_embed(q->g, r.tau, r.L, r.d, r.seed, r.out, &o, s);
+  if (st == IGP_OK) st = igp_graph_sync(q->g);
   if (st != IGP_OK) {
     q->status = st;
     q->error = igp_last_error();
