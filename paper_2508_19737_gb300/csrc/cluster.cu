@@ -87,24 +87,6 @@ __device__ __forceinline__ float dist2(const float (&x)[D], const float* __restr
   return s;
 }
 
-// Radius^2 2^32 of entry (n, LS, SS) merged with the point xq, in fp64 from the exact sums.
-template <int D>
-__device__ __forceinline__ double merged_r2(long long n, const long long* __restrict__ LS, unsigned long long SS,
-                                            const long long (&xq)[D]) {
-  unsigned long long ss = SS;
-#pragma unroll
-  for (int k = 0; k < D; ++k) ss += (unsigned long long)(xq[k] * xq[k]);
-  const double n1 = __ll2double_rn(n + 1);
-  const double r2 = __ddiv_rn(__ull2double_rn(ss), n1);
-  double b = 0.0;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    const double m = __ddiv_rn(__ll2double_rn(LS[k] + xq[k]), n1);
-    b = __dadd_rn(b, __dmul_rn(m, m));
-  }
-  return __dsub_rn(r2, b);
-}
-
 template <int D>
 __device__ __forceinline__ bool load_point(const float* __restrict__ E, int64_t i, float (&x)[D], long long (&xq)[D]) {
   bool ok = true;
@@ -142,9 +124,29 @@ __global__ void __launch_bounds__(kCluThreads) k_clu_best(const float* __restric
     for (int e = threadIdx.x; e < nt * D; e += kCluThreads) sc[e / D][e % D] = C[(int64_t)(t0 + e / D) * D + e % D];
     __syncthreads();
     if (p < m) {
-      for (int j = 0; j < nt; ++j) {
+      int j = 0;
+      for (; j + 4 <= nt; j += 4) {  // four entries' distances as independent chains, then in order
+        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float u0 = __fsub_rn(x[k], sc[j][k]), u1 = __fsub_rn(x[k], sc[j + 1][k]);
+          const float u2 = __fsub_rn(x[k], sc[j + 2][k]), u3 = __fsub_rn(x[k], sc[j + 3][k]);
+          s0 = __fadd_rn(s0, __fmul_rn(u0, u0));
+          s1 = __fadd_rn(s1, __fmul_rn(u1, u1));
+          s2 = __fadd_rn(s2, __fmul_rn(u2, u2));
+          s3 = __fadd_rn(s3, __fmul_rn(u3, u3));
+        }
+        const float dd[4] = {s0, s1, s2, s3};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (dd[q] < bd) {  // strict: the first (smallest id) minimum of the slice
+            bd = dd[q];
+            bc = t0 + j + q;
+          }
+      }
+      for (; j < nt; ++j) {
         const float dd = dist2<D>(x, sc[j]);
-        if (dd < bd) {  // strict: the first (smallest id) minimum of the slice
+        if (dd < bd) {
           bd = dd;
           bc = t0 + j;
         }
@@ -156,26 +158,48 @@ __global__ void __launch_bounds__(kCluThreads) k_clu_best(const float* __restric
 }
 
 // Step 2b: BIRCH's radius test against the closest entry (entries as at the start of the batch);
-// labels of the points that join, candidate flags (-1) of the others, and the input range check.
+// labels of the points that join, candidate flags (-1) of the others. The merged entry's
+// radius^2 2^32 is formed in fp64 from the exact integer sums: SS' / (n + 1) minus the sum over
+// coordinates, in order, of ((LS_k + xq_k) / (n + 1))^2. One warp per point: lane k takes
+// coordinates k, k + 32, ..; the integer sum of squares is exact in any order, and every lane adds
+// the squared means in coordinate order.
 template <int D>
-__global__ void __launch_bounds__(kCluThreads) k_clu_join(const float* __restrict__ E, int64_t b0, int m,
-                                                         const long long* __restrict__ n,
-                                                         const long long* __restrict__ LS,
-                                                         const unsigned long long* __restrict__ SS,
-                                                         const unsigned long long* __restrict__ best, double t2r,
-                                                         int32_t* __restrict__ lab, int32_t* __restrict__ ctr) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= m || ctr[2]) return;
-  float x[D];
-  long long xq[D];
-  load_point<D>(E, b0 + p, x, xq);
+__global__ void k_clu_join(const float* __restrict__ E, int64_t b0, int m, const long long* __restrict__ n,
+                           const long long* __restrict__ LS, const unsigned long long* __restrict__ SS,
+                           const unsigned long long* __restrict__ best, double t2r, int32_t* __restrict__ lab,
+                           int32_t* __restrict__ ctr) {
+  constexpr int KPL = (D + 31) / 32;  // coordinates per lane
+  const int p = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (p >= m || ctr[2]) return;  // warp-uniform
+  const unsigned long long bst = best[p];
   int l = -1;
-  const unsigned long long b = best[p];
-  if (b != kNoEntry) {
-    const int c = (int)(b & 0xffffffffu);
-    if (merged_r2<D>(n[c], LS + (int64_t)c * D, SS[c], xq) <= t2r) l = c;
+  if (bst != kNoEntry) {
+    const int c = (int)(bst & 0xffffffffu);
+    const double n1 = __ll2double_rn(n[c] + 1);
+    unsigned long long ss = 0;
+    double m2[KPL];
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+      const int k = lane + 32 * q;
+      m2[q] = 0.0;
+      if (k < D) {
+        const float vc = fminf(fmaxf(E[(b0 + p) * D + k], -1.0f), 1.0f);
+        const long long xq = qint(vc);
+        ss += (unsigned long long)(xq * xq);
+        const double mk = __ddiv_rn(__ll2double_rn(LS[(int64_t)c * D + k] + xq), n1);
+        m2[q] = __dmul_rn(mk, mk);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    double b = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) b = __dadd_rn(b, __shfl_sync(0xffffffffu, m2[k / 32], k % 32));
+    const double r2 = __ddiv_rn(__ull2double_rn(SS[c] + ss), n1);
+    if (__dsub_rn(r2, b) <= t2r) l = c;
   }
-  lab[p] = l;
+  if (lane == 0) lab[p] = l;
 }
 
 // Any coordinate outside [-1, 1] (or not finite) sets kErrRange; run over the whole input before
@@ -395,8 +419,7 @@ CluOps clu_ops() {
   o.join = [](const float* E, int64_t b0, int m, const long long* n, const long long* LS,
               const unsigned long long* SS, const unsigned long long* best, double t2r, int32_t* lab, int32_t* ctr,
               cudaStream_t s) {
-    k_clu_join<D><<<(m + kCluThreads - 1) / kCluThreads, kCluThreads, 0, s>>>(E, b0, m, n, LS, SS, best, t2r, lab,
-                                                                              ctr);
+    k_clu_join<D><<<(int)(((int64_t)m * 32 + 255) / 256), 256, 0, s>>>(E, b0, m, n, LS, SS, best, t2r, lab, ctr);
   };
   o.leaders = [](const float* E, int64_t b0, int m, const int32_t* cand, const int32_t* ctr, float t2d, int32_t* flag,
                  cudaStream_t s) {
@@ -431,7 +454,7 @@ bool get_clu_ops(int d, CluOps* o) {
 // Entry slices of the nearest-entry search: enough CTAs for about two per SM.
 int slices_for(int m) {
   const int pb = (m + kCluThreads - 1) / kCluThreads;
-  return std::max(1, std::min(64, (2 * num_sms() + pb - 1) / pb));
+  return std::max(1, std::min(64, (8 * num_sms() + pb - 1) / pb));  // about 8 CTAs per SM
 }
 
 // Device arrays for `need` entries (the first st.K kept, the rest zero).
