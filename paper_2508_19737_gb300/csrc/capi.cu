@@ -71,6 +71,32 @@ static cudaMemPool_t pool_for_current_device() {
   return g_pools[dev];
 }
 
+static std::mutex g_slot_mu;
+static std::vector<int*> g_slots;
+constexpr int kSlotInts = 16;   // 64 bytes a slot
+constexpr int kSlabSlots = 256; // slots page-locked at a time
+
+int* pinned_slot() {
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  if (g_slots.empty()) {
+    int* slab = nullptr;
+    if (cudaHostAlloc((void**)&slab, (size_t)kSlabSlots * kSlotInts * sizeof(int), cudaHostAllocDefault) !=
+        cudaSuccess)
+      return nullptr;
+    for (int k = kSlabSlots - 1; k >= 0; --k) g_slots.push_back(slab + (size_t)k * kSlotInts);
+  }
+  int* w = g_slots.back();
+  g_slots.pop_back();
+  memset(w, 0, kSlotInts * sizeof(int));
+  return w;
+}
+
+void release_slot(int* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  g_slots.push_back(p);
+}
+
 igp_status dev_alloc(void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
   cudaMemPool_t pool = pool_for_current_device();
@@ -241,7 +267,7 @@ igp_status igp_graph_build_profiled(const int32_t* src, const int32_t* dst, int6
   cudaGetDevice(&g->device);
   count_alloc();
   if (cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess ||
-      cudaHostAlloc((void**)&g->err_host, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+      (g->err_host = pinned_slot()) == nullptr) {
     igp_status e = cuda_status(cudaGetLastError(), "graph handle set-up", __FILE__, __LINE__);
     if (g->done) cudaEventDestroy(g->done);
     delete g;
@@ -261,7 +287,7 @@ igp_status igp_graph_build_profiled(const int32_t* src, const int32_t* dst, int6
   if (st == IGP_OK) st = graph_mark(g, s);
   if (st != IGP_OK) {
     cudaEventDestroy(g->done);
-    cudaFreeHost(g->err_host);
+    release_slot(g->err_host);  // the failed build copied nothing into it
     delete g;
     return st;
   }
@@ -367,7 +393,7 @@ void igp_graph_free(igp_graph* g) {
     cudaEventSynchronize(g->done);  // the pinned error word may still be written
     cudaEventDestroy(g->done);
   }
-  if (g->err_host) cudaFreeHost(g->err_host);
+  release_slot(g->err_host);  // after the handle's last work
   cudaGetLastError();
   if (cur != g->device) cudaSetDevice(cur);
   delete g;
@@ -509,7 +535,7 @@ static void batch_release(igp_batch* b) {
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   if (b->ev_err) cudaEventDestroy(b->ev_err);
-  if (b->err_host) cudaFreeHost(b->err_host);
+  release_slot(b->err_host);  // after the device synchronisation above
   cudaGetLastError();
   delete b;
 }

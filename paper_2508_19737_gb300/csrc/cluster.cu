@@ -560,8 +560,8 @@ igp_status igp_clusterer_create(int32_t d, double threshold, int32_t batch, int3
     st.lab = st.eid + B;
     st.ctr = st.lab + B;
     count_alloc();
-    if (cudaHostAlloc((void**)&st.ctr_host, 16, cudaHostAllocDefault) != cudaSuccess) {
-      e = cuda_status(cudaGetLastError(), "cudaHostAlloc", __FILE__, __LINE__);
+    if ((st.ctr_host = pinned_slot()) == nullptr) {
+      e = cuda_status(cudaGetLastError(), "page-locked counters", __FILE__, __LINE__);
       dev_free(p, 0);
     }
   }
@@ -587,7 +587,7 @@ void igp_clusterer_free(igp_clusterer* c) {
   dev_free(st.SS, 0);
   dev_free(st.C, 0);
   dev_free(st.best, 0);
-  if (st.ctr_host) cudaFreeHost(st.ctr_host);
+  release_slot(st.ctr_host);  // after the synchronisation above
   delete c;
 }
 

@@ -2509,8 +2509,8 @@ igp_status batch_embed(igp_batch* b, double tau, int32_t L, int32_t d, const uin
   }
   if (!b->err_host) {
     count_alloc();
-    IGP_TRY_CUDA(cudaHostAlloc((void**)&b->err_host, sizeof(int), cudaHostAllocDefault));
-    *b->err_host = 0;
+    b->err_host = pinned_slot();
+    if (!b->err_host) return cuda_status(cudaGetLastError(), "page-locked error word", __FILE__, __LINE__);
   }
   char* base = (char*)b->ws;
   void* T0 = base;

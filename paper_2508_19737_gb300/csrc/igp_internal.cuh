@@ -43,6 +43,12 @@ void count_launches(int64_t n);
 igp_status dev_alloc(void** p, size_t bytes, cudaStream_t s);
 // Count one memory allocation (igp_alloc_count); dev_alloc counts its own.
 void count_alloc();
+// A zeroed 64-byte page-locked host slot (16 ints) for flags and small readbacks, from a free list
+// that keeps slots for the life of the process (cudaFreeHost would synchronise the whole device, so
+// releasing a graph handle would wait for the work of every other). NULL if page-locking fails.
+int* pinned_slot();
+// Back to the free list; the caller makes sure no copy into the slot is still pending.
+void release_slot(int* p);
 void dev_free(void* p, cudaStream_t s);
 // Bytes the current device's library pool holds but does not use (free for dev_alloc).
 size_t pool_idle_bytes();

@@ -99,15 +99,14 @@ extern "C" igp_status igp_graph_import(const int32_t* row_ptr, const int32_t* co
     dev_free(cl, s);
     dev_free(tmp, s);
     cudaStreamSynchronize(s);
-    if (host) cudaFreeHost(host);
+    release_slot(host);  // the stream has drained: no copy is pending
     if (g->done) cudaEventDestroy(g->done);
-    if (g->err_host) cudaFreeHost(g->err_host);
+    release_slot(g->err_host);
     delete g;
     return e;
   };
   if (cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming) != cudaSuccess ||
-      cudaHostAlloc((void**)&g->err_host, sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
-      cudaHostAlloc((void**)&host, 2 * sizeof(int), cudaHostAllocDefault) != cudaSuccess)
+      (g->err_host = pinned_slot()) == nullptr || (host = pinned_slot()) == nullptr)
     return fail(cuda_status(cudaGetLastError(), "graph handle set-up", __FILE__, __LINE__));
   *g->err_host = 0;
   const size_t bp = ((size_t)N + 1) * sizeof(int32_t), bc = (size_t)nnz * sizeof(int32_t);
@@ -140,7 +139,7 @@ extern "C" igp_status igp_graph_import(const int32_t* row_ptr, const int32_t* co
   g->row_ptr = (int32_t*)rp;
   g->col = (int32_t*)cl;
   dev_free(tmp, s);
-  cudaFreeHost(host);
+  release_slot(host);  // read after the stream synchronisation above
   if (cudaEventRecord(g->done, s) != cudaSuccess) {
     rp = cl = tmp = nullptr;
     host = nullptr;
