@@ -80,7 +80,8 @@ int* pinned_slot() {
   std::lock_guard<std::mutex> lk(g_slot_mu);
   if (g_slots.empty()) {
     int* slab = nullptr;
-    if (cudaHostAlloc((void**)&slab, (size_t)kSlabSlots * kSlotInts * sizeof(int), cudaHostAllocDefault) !=
+    // portable: a slot may serve a handle on any device of the process
+    if (cudaHostAlloc((void**)&slab, (size_t)kSlabSlots * kSlotInts * sizeof(int), cudaHostAllocPortable) !=
         cudaSuccess)
       return nullptr;
     for (int k = kSlabSlots - 1; k >= 0; --k) g_slots.push_back(slab + (size_t)k * kSlotInts);
