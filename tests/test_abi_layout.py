@@ -46,3 +46,12 @@ def test_ctypes_structs_match_the_c_header(tmp_path):
         assert ctypes.sizeof(py) == layout[(cname, "sizeof")], cname
         for f, _ in py._fields_:
             assert getattr(py, f).offset == layout[(cname, f)], (cname, f)
+
+
+def test_embed_opts_defaults_and_host_async():
+    """igp_embed_opts_init (host code, no GPU needed) leaves host_async at 0: a host output is
+    final when igp_embed returns unless the caller asks otherwise; the binding sets it on request."""
+    from paper_2508_19737_gb300 import api
+    assert api.embed_opts().host_async == 0
+    o = api.embed_opts(host_async=True, storage="bf16")
+    assert o.host_async == 1 and o.storage == api.STORAGE["bf16"] and o.alpha == 1.0 and o.theta == 0.1
