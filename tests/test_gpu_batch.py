@@ -160,21 +160,25 @@ def test_persistent_launch_equals_per_layer_launches(api, d, storage):
     """The persistent plan (all layers in one cooperative launch, each graph advancing past its own
     statistics) computes exactly what the per-layer plan computes: the same rows in the same order,
     the same exact integer statistics. Checked bit for bit, for both claim sizes and CTA counts,
-    plus the launch count of a persistent embedding (Theta, one launch for the layers, output)."""
+    plus the launch count of a persistent embedding (Theta, one launch for the layers, output).
+    A star (one row of 6,000 entries) makes the work-balanced chunk table give its hub tile a chunk
+    of its own; claims of 32, 64 and 256 positions on average use three different tables."""
     import torch
-    edges = _graphs() + [(g.src, g.dst, g.N) for g in (synth.dcsbm(20011, 16, 25, 2.3, 5, seed=9),
-                                                       synth.dcsbm(7000, 8, 12, 2.5, 5, seed=10))]
+    star = (np.zeros(6000, np.int32), np.arange(1, 6001, dtype=np.int32), 6001)
+    edges = _graphs() + [star] + [(g.src, g.dst, g.N) for g in (synth.dcsbm(20011, 16, 25, 2.3, 5, seed=9),
+                                                                 synth.dcsbm(7000, 8, 12, 2.5, 5, seed=10))]
     graphs = [api.graph_build(s, t, n) for s, t, n in edges]
     batch = api.Batch(graphs)
     G, N, _, offs = batch.info()
     seeds = [3 * k + 2 for k in range(G)]
     outs = {}
-    for hook in (5, 3, 4):
+    for hook in (5, 3, 4, 6, 7):
         o = torch.full((N, d), -1.0, dtype=torch.float32, device="cuda")
         batch.embed(-0.5, 10, d, seeds, out=o, storage=storage, reserved_test=hook)
         batch.sync()
         outs[hook] = o
-    assert torch.equal(outs[3], outs[5]) and torch.equal(outs[4], outs[5])
+    for hook in (3, 4, 6, 7):
+        assert torch.equal(outs[hook], outs[5]), hook
     n0 = api.launch_count()
     batch.embed(-0.5, 10, d, seeds, out=outs[3], storage=storage, reserved_test=3)
     batch.sync()
