@@ -191,7 +191,9 @@ def test_persistent_launch_equals_per_layer_launches(api, d, storage):
     if storage == "f32":
         assert _rel(got, ref) <= TOL["f32"]
     else:
-        check_bf16(got, rp, col, oracle.theta_input(seeds[k], n, d), -0.5, 10, strict=True)
+        # the batch graphs' criterion (tau < 0 amplifies a few rows beyond what bf16 storage keeps
+        # within 2e-2 of FP64; the kernel must still follow the storage model on every row)
+        check_bf16(got, rp, col, oracle.theta_input(seeds[k], n, d), -0.5, 10)
     batch.free()
     for g in graphs:
         g.free()
