@@ -244,6 +244,44 @@ def test_eq3_spectral_equals_spatial(tau, alpha, theta):
     np.testing.assert_allclose(spatial, spectral, atol=1e-10)
 
 
+@pytest.mark.parametrize("tau", [0.0, 2.5, -1.5, -10.0])
+def test_regular_graph_normalized_adjacency_of_ones(tau):
+    """On a d-regular graph every D_tau is the same number c (Eq. 1: d + tau for tau >= 0, and
+    d - min(|tau|, d - eps) for tau < 0), so D_tau^{-1/2} A D_tau^{-1/2} 1 = (d / c) 1."""
+    N, offs = 30, (1, 2, 5)  # circulant: node i joined to i +- 1, 2, 5, so d = 6
+    src = np.array([i for i in range(N) for _ in offs])
+    dst = np.array([(i + o) % N for i in range(N) for o in offs])
+    row_ptr, col = oracle.build_csr(src, dst, N)
+    d = 2 * len(offs)
+    assert np.all(np.diff(row_ptr) == d)
+    c = d + tau if tau >= 0 else d - min(abs(tau), d - 1e-3)
+    dinv = oracle.inv_sqrt_degrees(oracle.degree_correction(oracle.degrees(row_ptr), tau))
+    Ahat = oracle.normalized_adjacency(row_ptr, col, dinv)
+    np.testing.assert_allclose(Ahat @ np.ones(N), np.full(N, d / c), rtol=1e-14)
+
+
+@pytest.mark.parametrize("tau", [-1.5, -0.5, 0.0, 3.0])
+def test_ffp_through_the_spectral_form_equals_the_oracle(tau):
+    """Alg. 1 written with the spectral form of Eq. 3 at every layer (an eigendecomposition of
+    L_tau, the filter of Eq. 2 on its eigenvalues), numpy's column mean and sample standard
+    deviation for ZNorm and scipy's logistic function for the output, against the oracle's
+    spatial FFP: the assembly of Eq. 4's steps must agree, not only one convolution."""
+    from scipy.special import expit
+    rng = np.random.default_rng(5)
+    N, d, L, alpha, theta = 36, 6, 4, 1.0, 0.1
+    src = rng.integers(0, N, 110)
+    dst = rng.integers(0, N, 110)
+    row_ptr, col = oracle.build_csr(src, dst, N)
+    lam, U = np.linalg.eigh(oracle.corrected_laplacian(oracle.dense_adjacency(row_ptr, col), tau))
+    phi = (theta + alpha) - alpha * lam
+    X = rng.standard_normal((N, d)) / math.sqrt(d)
+    Z = X
+    for _ in range(L):
+        T = np.tanh(U @ (phi[:, None] * (U.T @ Z)))
+        Z = (T - T.mean(axis=0)) / T.std(axis=0, ddof=1)
+    np.testing.assert_allclose(oracle.ffp(row_ptr, col, X, tau, L), expit(Z), atol=1e-11)
+
+
 # ---------------------------------------------------------------------------
 # Eq. 4 and Alg. 1 on hand-worked cases
 # ---------------------------------------------------------------------------
