@@ -783,7 +783,11 @@ def e2e_measure(api, torch, ctx, steps, world, barrier=lambda: None):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     return {"value": replica_rate(ctx["units_step"], steps, world, e2e_s * 1e3), "unit": UNIT,
             "h2d_bytes_per_step": 2 * 4 * M, "d2h_bytes_per_step": N * d * 4, "steps": steps,
-            "streams": 2}
+            "streams": 2,
+            "pipeline": "per step: pinned host edges copied to a device buffer on the step's stream "
+                        "(issued before the previous step's embedding), igp_graph_build on them, "
+                        "igp_embed into pinned host memory with opts.host_async, igp_graph_sync of the "
+                        "previous step; two streams alternate"}
 
 
 def extras(api, torch, args, local):
