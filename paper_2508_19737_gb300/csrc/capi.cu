@@ -382,7 +382,8 @@ void igp_graph_free(igp_graph* g) {
   int cur = 0;
   cudaGetDevice(&cur);
   if (cur != g->device) cudaSetDevice(g->device);
-  // stream-ordered release after the handle's last work; no host synchronisation
+  // device memory: released in stream order after the handle's last work; the host then waits for
+  // that work only because the handle's page-locked error word may be written until it ends
   cudaStream_t s = cudaStreamPerThread;
   if (g->done) cudaStreamWaitEvent(s, g->done, 0);
   if (g->row_ptr) cudaFreeAsync(g->row_ptr, s);
